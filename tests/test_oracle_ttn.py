@@ -1,0 +1,85 @@
+"""Pins of the oracle's TTN sweep: the exact two-site energy, exactness
+against independent ED at sufficient bond dimension on 2x2x1, the
+variational bound below it, and the invariants (isometry, charge, Gauss sum
+rule, centre independence, monotone energy)."""
+import numpy as np
+import pytest
+
+from oracle import ed, model, ttn
+
+
+def test_single_node_closed_form():
+    p = model.Params(2, 1, 1, t=1.0, m=1.0, ge2=1.0, cB=0.5, nu=10.0, Q=0)
+    s = ttn.TTN(p, 8, 0)
+    e = s.sweep(tol=1e-12)
+    assert abs(e[-1] - (0.25 - np.sqrt(41.0) / 4.0)) < 1e-10
+
+
+@pytest.fixture(scope="module")
+def swept_2x2x1():
+    p = model.Params(2, 2, 1, t=1.0, m=1.0, ge2=1.0, cB=0.5, nu=10.0, Q=0)
+    s = ttn.TTN(p, 12, 0)
+    energies = s.sweep(tol=1e-10)
+    return p, s, energies
+
+
+def test_reaches_exact_diagonalisation(swept_2x2x1):
+    p, s, energies = swept_2x2x1
+    e_ed = ed.config_ed(p)
+    assert abs(energies[-1] - e_ed) < 1e-9 * abs(e_ed)
+
+
+def test_variational_bound_small_chi():
+    p = model.Params(2, 2, 1, t=1.0, m=1.0, ge2=1.0, cB=0.5, nu=10.0, Q=0)
+    s = ttn.TTN(p, 4, 1)
+    e = s.sweep(tol=1e-10)
+    assert e[-1] > ed.config_ed(p) + 1e-3
+
+
+def test_energy_monotone(swept_2x2x1):
+    _, _, energies = swept_2x2x1
+    assert all(b <= a + 1e-9 for a, b in zip(energies, energies[1:]))
+
+
+def test_isometry_and_centre_independence(swept_2x2x1):
+    p, s, energies = swept_2x2x1
+    e_root = s.energy_at_center()
+    assert abs(e_root - energies[-1]) < 1e-9
+    for target in (0, 1, 2):
+        s.move_to(target)
+        assert abs(s.energy_at_center() - e_root) < 1e-10
+        assert abs(s.norm_at_center() - 1.0) < 1e-12
+        for nd in s.nodes:
+            if nd.index == s.center:
+                continue
+            T = s.T[nd.index]
+            leg = s._neighbour_leg(nd.index, s.path(nd.index, s.center)[1])
+            A = np.moveaxis(T, leg, 2).reshape(-1, T.shape[leg])
+            np.testing.assert_allclose(A.T @ A, np.eye(A.shape[1]), atol=1e-12)
+
+
+def test_charge_and_gauss_sum_rule(swept_2x2x1):
+    p, s, _ = swept_2x2x1
+    obs = s.observables()
+    assert abs(obs["Q"] - p.Q) < 1e-12
+    lat = s.lat
+    # Q - sum <dangling outflow> = sum_links <2 - L>  (sum of Eq. (11) over sites)
+    flux = 0.0
+    for x in range(lat.n_sites):
+        for j in lat.dangling(x):
+            flux += 1.0 - obs["k"][x][j]
+    links = sum(2.0 - obs["k"][x][model.plus(mu)] - obs["k"][y][model.minus(mu)] for (x, mu, y) in lat.links())
+    assert abs((p.Q - flux) - links) < 1e-12
+    assert obs["delta_L"] < 1e-2
+    assert 0.0 <= obs["rho"] <= 1.0
+
+
+def test_energy_split_by_class(swept_2x2x1):
+    """E is linear in the couplings at fixed psi (Eq. (1) + (16)):
+    sum_class <H_class> + nu N_links = <H>."""
+    p, s, energies = swept_2x2x1
+    total = ttn.expectation(s, p)
+    parts = sum(ttn.expectation(s, model.class_only(p, c)) for c in ("t", "m", "ge2", "cB"))
+    pen = ttn.expectation(s, model.class_only(p, "nu"))
+    assert abs(total - energies[-1]) < 1e-9
+    assert abs(parts + pen - total) < 1e-10
