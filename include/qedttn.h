@@ -1,0 +1,178 @@
+/*
+ * qedttn: GB300 (sm_103a) hot path of the Tree Tensor Network ground-state
+ * search for compact (3+1)D lattice QED of Magnifico, Felser, Silvi and
+ * Montangero, "Lattice Quantum Electrodynamics in (3+1)-dimensions at finite
+ * density with Tensor Networks" (arXiv:2011.10658).
+ *
+ * The library builds the problem the paper states -- the gauge-invariant
+ * dressed-site basis (Methods, Eq. (12)-(14)), the Hamiltonian of Eq. (1)
+ * written as products of local operators (Eq. (15) and the plaquette
+ * factorisation) plus the link penalty of Eq. (16), in a fixed total-charge
+ * sector -- and sweeps a U(1)-symmetric binary TTN (Methods, "Tensor
+ * Networks": H_eff of one tensor, its lowest eigenpair by a Krylov method,
+ * tensor update, sweeping from the lowest to the highest layer).
+ *
+ * Conventions
+ *  - Return value: a qed_status (0 = success, negative = error).  After an
+ *    error, qed_last_error() returns a message (thread-local).
+ *  - Opaque handles are owned by the library and freed by the *_destroy
+ *    functions.  Output buffers are owned by the caller; sizes are counted in
+ *    elements; passing a NULL buffer (or cap = 0) queries the size in *n.
+ *  - Host pointers unless the name says "device".  The stream passed to
+ *    ttn_create is used for every kernel of that state; calls that return
+ *    host values synchronise that stream.  One state per thread at a time.
+ *  - No C++ exception crosses this boundary.
+ */
+#ifndef QEDTTN_H
+#define QEDTTN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Couplings and lattice of Eq. (1) + Eq. (16).  The couplings are taken as
+ * independent inputs (Results, "The model": the numerical setup treats t, m,
+ * g_e, g_m as mutually independent).  The plaquette term enters as
+ * -cB * sum(box + h.c.), i.e. cB = g_m^2 / 2.  nu is the link-constraint
+ * penalty of Eq. (16).  Q is the total charge sum_x (psi^dag psi -
+ * (1 - (-1)^x)/2) (Eq. (1) text).  boundary: 0 = open, every site keeps its
+ * six half-links and the ones pointing out of the lattice are free
+ * ("dangling", each costing ge2/2 (1 - k)^2); other values are rejected. */
+typedef struct {
+  int32_t Lx, Ly, Lz;
+  int32_t boundary;
+  double t, m, ge2, cB, nu;
+  int32_t Q;
+} qed_params;
+
+typedef enum {
+  QED_OK = 0,
+  QED_EINVAL = -1,      /* invalid argument */
+  QED_ENOMEM = -2,      /* device or host allocation failed */
+  QED_ECUDA = -3,       /* CUDA runtime error */
+  QED_ENOCONV = -4,     /* eigensolver stopped above tolerance; result valid */
+  QED_ENAN = -5,        /* non-finite input or rank-deficient factorisation */
+  QED_ETIMEOUT = -6,    /* a device wait hit its iteration limit */
+  QED_EUNSUPPORTED = -7 /* configuration outside what this build supports */
+} qed_status;
+
+enum { QED_PREC_FP64 = 0, QED_PREC_TF32 = 1, QED_PREC_BF16 = 2 };
+
+/* Local operator kinds of qed_local_op (half-link index j: 0..5 for
+ * -x, -y, -z, +x, +y, +z). */
+enum {
+  QED_OP_IDENTITY = 0,
+  QED_OP_M = 1,    /* psi^dag eta_j        (Eq. (15))          */
+  QED_OP_MD = 2,   /* eta_j^dag psi        (Eq. (15))          */
+  QED_OP_C = 3,    /* eta_i^dag eta_j      (plaquette factor)  */
+  QED_OP_P = 4,    /* projector on k_j = k (Eq. (16))          */
+  QED_OP_N = 5,    /* psi^dag psi          (mass term)         */
+  QED_OP_E2 = 6    /* sum over mask j of (1 - k_j)^2, Eq. (10) squared; j1 = bit mask */
+};
+
+typedef struct qed_model qed_model;
+typedef struct ttn_state ttn_state;
+
+/* Dressed-site basis of Eq. (12)-(14) for parity +1 (even) or -1 (odd).
+ * table: [267][9] int8 rows (phi, k1..k6, sign of Eq. (12), charge q);
+ * rows ordered phi outer, then (k1..k6) lexicographic.  NULL table: only
+ * *n_rows is written.  Errors: QED_EINVAL for another parity. */
+int qed_basis(int parity, int8_t *table, int32_t *n_rows);
+
+/* Local operator in monomial form on a site of the given parity:
+ * (O v)[i] = val[i] * v[src[i]], src[i] = -1 for a zero row.  src[267],
+ * val[267] caller-owned.  For QED_OP_C, j1 = i and j2 = j; for QED_OP_P,
+ * j1 = j and j2 = k; for QED_OP_E2, j1 = bit mask.  Built from the rishon
+ * algebra of Eq. (6) with Jordan-Wigner signs inside the site. */
+int qed_local_op(int parity, int op_kind, int j1, int j2, int16_t *src, double *val);
+
+/* Model: lattice, product-term list of Eq. (1) + (16), binary tree (Methods,
+ * "Tensor Networks": x-pairs, then y, then z, repeating).  Lattice extents
+ * must be powers of two with at least two sites. */
+int qed_model_create(const qed_params *p, qed_model **out);
+void qed_model_destroy(qed_model *m);
+/* n_sites, number of product terms, number of tree nodes, additive constant
+ * nu * N_links of Eq. (16). */
+int qed_model_info(const qed_model *m, int32_t *n_sites, int32_t *n_terms, int32_t *n_nodes, double *constant);
+/* Term list: for term i, coef[i], cls[i] (0 t, 1 m, 2 ge2, 3 cB, 4 nu) and up
+ * to four factors ops[i][f] = (site, kind, a, b) with n_ops[i] factors. */
+int qed_model_terms(const qed_model *m, double *coef, int32_t *cls, int32_t *n_ops, int32_t *ops /* [n][4][4] */,
+                    int64_t cap, int64_t *n);
+/* Tree: per node (layer, axis, child_kind0, child0, child_kind1, child1,
+ * parent); child_kind 0 = site, 1 = node; parent -1 for the root. */
+int qed_model_tree(const qed_model *m, int32_t *nodes /* [n][7] */, int64_t cap, int64_t *n);
+/* Bond sector table for bond dimension chi: for the bond above each node,
+ * its sectors as consecutive (node, q, dim) triples. */
+int qed_model_sectors(const qed_model *m, int32_t chi, int32_t *triples, int64_t cap, int64_t *n);
+
+/* TTN state on the current CUDA device.  Tensors start as SplitMix64-seeded
+ * random isometries (per-sector QR with positive diag R), the centre at the
+ * root, all renormalized operators built.  precision: QED_PREC_*.
+ * cuda_stream: a cudaStream_t (NULL = the legacy default stream). */
+int ttn_create(const qed_model *m, int32_t chi, uint64_t seed, int precision, void *cuda_stream, ttn_state **out);
+void ttn_destroy(ttn_state *s);
+
+typedef struct {
+  double energy;            /* last eigenvalue (penalty and constant included) */
+  int32_t matvecs;          /* H_eff applications */
+  int32_t node_updates;
+  int32_t not_converged;    /* node updates that stopped above tolerance */
+  double max_rel_residual;  /* max |beta_k s_k| / |theta| */
+  double seconds;           /* wall time of the call */
+} ttn_sweep_stats;
+
+/* n_sweeps full sweeps: nodes in number order (layer by layer from the
+ * bottom), the centre moved along the tree with per-sector QR, each node
+ * replaced by the lowest eigenvector of its H_eff (Lanczos with full
+ * reorthogonalisation, started from the current tensor, stopping at
+ * residual <= tol |theta|, restarted every max_krylov steps).
+ * Returns QED_ENOCONV (stats still valid) if some update stopped early. */
+int ttn_sweep(ttn_state *s, int32_t n_sweeps, double tol, int32_t max_krylov, ttn_sweep_stats *out);
+/* Optimise one node (moving the centre there first). */
+int ttn_optimize_node(ttn_state *s, int32_t node, double tol, int32_t max_krylov, double *energy);
+/* Move the isometry centre to a node. */
+int ttn_move_center(ttn_state *s, int32_t node);
+int ttn_info(ttn_state *s, int32_t *center, int32_t *n_nodes, int64_t *max_node_size);
+int ttn_node_size(ttn_state *s, int32_t node, int64_t *n);
+
+/* <H + H_pen> of the state (constant included) and the same without the
+ * penalty; E_class[5] (nullable) = <H_class> per coupling class t, m, ge2,
+ * cB, nu (constant in the nu class), i.e. dE/dc_class times c_class. */
+int ttn_energy(ttn_state *s, double *E_total, double *E_without_penalty, double *E_class);
+
+/* Observables (Results text and Eq. (16a), (17b)), centre moved to the root:
+ *  QED_MEAS_PROBS  : [N_sites][267] diagonal of each single-site reduced
+ *                    density matrix
+ *  QED_MEAS_PHI    : [N_sites] <psi^dag psi>
+ *  QED_MEAS_NX     : [N_sites] n_x = (1 + p)/2 - p <psi^dag psi>
+ *  QED_MEAS_QX     : [N_sites] <q_x>
+ *  QED_MEAS_K      : [N_sites][6] <k_j>
+ *  QED_MEAS_ELINK  : [N_links] <E> on each internal link (Eq. (10))
+ *  QED_MEAS_SCALARS: [4] rho, delta_L, sum_x <q_x>, number of sigma layers
+ *  QED_MEAS_SIGMA  : [layers] sigma(l), l = 1.. distance to the boundary */
+enum {
+  QED_MEAS_PROBS = 0, QED_MEAS_PHI = 1, QED_MEAS_NX = 2, QED_MEAS_QX = 3, QED_MEAS_K = 4,
+  QED_MEAS_ELINK = 5, QED_MEAS_SCALARS = 6, QED_MEAS_SIGMA = 7
+};
+int ttn_measure(ttn_state *s, int kind, double *out, int64_t cap, int64_t *n);
+
+/* Copy of one node tensor in its block layout (FP64): blocks ordered by
+ * (parent sector, left charge), each block row-major (left, right, parent). */
+int ttn_node_export(ttn_state *s, int32_t node, double *buf, int64_t cap, int64_t *n);
+/* Replace one node tensor (same layout).  QED_ENAN on non-finite input. */
+int ttn_node_import(ttn_state *s, int32_t node, const double *buf, int64_t n);
+
+/* y = H_eff x at the current centre (Methods step (i)), x and y in the
+ * centre's block layout; host buffers (copied in and out). */
+int ttn_apply_heff(ttn_state *s, const double *x, double *y, int64_t n);
+/* Same with device buffers on the state's stream (no host copies). */
+int ttn_apply_heff_device(ttn_state *s, const double *x_device, double *y_device, int64_t n);
+
+const char *qed_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QEDTTN_H */

@@ -235,3 +235,62 @@ def qr_positive(M):
     d = np.sign(np.diag(R))
     d[d == 0] = 1.0
     return Qm * d[None, :], R * d[:, None]
+
+
+# Rank handling of the centre-move QR (a reading: the paper keeps the bond
+# dimensions fixed only implicitly).  A sector matrix whose QR diagonal
+# falls below QR_FALLBACK * (largest column norm) is factorised by
+# classical Gram-Schmidt applied twice per column; a column whose remainder
+# is at most QR_DEPENDENT * (largest column norm) is dependent: R_jj = 0 and
+# q_j is the first unit vector e_k (k increasing over the rows, never reused)
+# whose remainder after two projections exceeds QR_ACCEPT.
+QR_FALLBACK = 1e-6
+QR_DEPENDENT = 1e-9
+QR_ACCEPT = 0.5
+
+
+def qr_gram_schmidt(X):
+    """Column-by-column Gram-Schmidt (two passes) with deterministic
+    completion of dependent columns; returns Q (orthonormal columns), R."""
+    m, n = X.shape
+    if n > m:
+        raise ValueError("sector has fewer rows than columns")
+    Q = np.zeros((m, n))
+    R = np.zeros((n, n))
+    scale = max(float(np.max(np.linalg.norm(X, axis=0))), 0.0) if n else 0.0
+    next_k = 0
+    for j in range(n):
+        v = X[:, j].copy()
+        for _ in range(2):
+            c = Q[:, :j].T @ v
+            v = v - Q[:, :j] @ c
+            R[:j, j] += c
+        nv = float(np.linalg.norm(v))
+        if nv > QR_DEPENDENT * scale:
+            Q[:, j] = v / nv
+            R[j, j] = nv
+            continue
+        while True:
+            w = np.zeros(m)
+            w[next_k] = 1.0
+            next_k += 1
+            for _ in range(2):
+                w = w - Q[:, :j] @ (Q[:, :j].T @ w)
+            nw = float(np.linalg.norm(w))
+            if nw > QR_ACCEPT:
+                Q[:, j] = w / nw
+                break
+    return Q, R
+
+
+def qr_sector(X):
+    """QR of one sector matrix for a centre move: the unique QR with
+    positive diag(R) when every diagonal entry exceeds QR_FALLBACK times the
+    largest column norm, else ``qr_gram_schmidt``."""
+    if X.shape[1] > X.shape[0]:
+        raise ValueError("sector has fewer rows than columns")
+    Qm, R = qr_positive(X)
+    scale = float(np.max(np.linalg.norm(X, axis=0))) if X.size else 0.0
+    if X.shape[1] and np.min(np.abs(np.diag(R))) <= QR_FALLBACK * scale:
+        return qr_gram_schmidt(X)
+    return Qm, R

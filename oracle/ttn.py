@@ -19,8 +19,10 @@ operators are dense bond x bond matrices.  Physical site operators are
 scipy CSR matrices from ``oracle.fock``.
 
 Gauge: all tensors except the centre are isometries pointing at the
-centre.  Moving the centre across a bond is a per-sector QR with positive
-diag(R) (``tree.qr_positive``); R is absorbed by the neighbour.
+centre.  Moving the centre across a bond is a per-sector QR
+(``tree.qr_sector``: positive diag(R), with a deterministic completion of
+rank-deficient sectors); R is absorbed by the neighbour.  Rows of a sector
+matrix are ordered lexicographically in the two other legs.
 
 Bond operators: ``up[n]`` holds, for the bond above node n, the
 renormalized restriction to subtree(n) of every term that crosses the bond
@@ -291,7 +293,7 @@ class TTN:
             A = Tm[rows[0], rows[1], :][:, cols]
             if A.shape[0] < A.shape[1]:
                 raise ValueError("sector has fewer rows than columns")
-            Qm, Rq = _tree.qr_positive(A)
+            Qm, Rq = _tree.qr_sector(A)
             newT[rows[0][:, None], rows[1][:, None], cols[None, :]] = Qm
             R[np.ix_(cols, cols)] = Rq
         self.T[idx] = np.moveaxis(newT, 2, leg)

@@ -1,0 +1,176 @@
+"""GB300-native TTN hot path for (3+1)D lattice QED (arXiv:2011.10658).
+
+Thin Python layer over the C ABI of include/qedttn.h.  Every computation
+runs in libqedttn.so (host model code and sm_103a kernels); this module only
+marshals arguments.
+"""
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import QedError, QedParams, SweepStats, check, lib
+
+PREC = {"fp64": 0, "tf32": 1, "bf16": 2}
+OP = {"I": 0, "M": 1, "MD": 2, "C": 3, "P": 4, "N": 5, "E2": 6}
+MEAS = {"probs": 0, "phi": 1, "nx": 2, "qx": 3, "k": 4, "elink": 5, "scalars": 6, "sigma": 7}
+CLASSES = ("t", "m", "ge2", "cB", "nu")
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def basis(parity):
+    """Dressed-site basis table [267, 9] (phi, k1..k6, sign, q)."""
+    out = np.zeros((267, 9), dtype=np.int8)
+    n = ctypes.c_int32()
+    check(lib().qed_basis(parity, _ptr(out, ctypes.c_int8), ctypes.byref(n)))
+    return out[: n.value]
+
+
+def local_op(parity, kind, j1=0, j2=0):
+    """Monomial site operator: (src[267] int16, val[267] float64)."""
+    src = np.zeros(267, dtype=np.int16)
+    val = np.zeros(267, dtype=np.float64)
+    k = OP[kind] if isinstance(kind, str) else int(kind)
+    check(lib().qed_local_op(parity, k, j1, j2, _ptr(src, ctypes.c_int16), _ptr(val, ctypes.c_double)))
+    return src, val
+
+
+class Model:
+    """Lattice, term list and tree (qed_model_create)."""
+
+    def __init__(self, Lx, Ly, Lz, t=1.0, m=1.0, ge2=1.0, cB=0.5, nu=10.0, Q=0, boundary=0):
+        self.params = QedParams(Lx, Ly, Lz, boundary, t, m, ge2, cB, nu, Q)
+        h = ctypes.c_void_p()
+        check(lib().qed_model_create(ctypes.byref(self.params), ctypes.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().qed_model_destroy(h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        ns, nt, nn = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        c = ctypes.c_double()
+        check(lib().qed_model_info(self._h, ctypes.byref(ns), ctypes.byref(nt), ctypes.byref(nn), ctypes.byref(c)))
+        return dict(n_sites=ns.value, n_terms=nt.value, n_nodes=nn.value, constant=c.value)
+
+    def terms(self):
+        n = ctypes.c_int64()
+        check(lib().qed_model_terms(self._h, None, None, None, None, 0, ctypes.byref(n)))
+        cnt = n.value
+        coef = np.zeros(cnt)
+        cls = np.zeros(cnt, dtype=np.int32)
+        nops = np.zeros(cnt, dtype=np.int32)
+        ops = np.zeros((cnt, 4, 4), dtype=np.int32)
+        check(lib().qed_model_terms(self._h, _ptr(coef, ctypes.c_double), _ptr(cls, ctypes.c_int32),
+                                    _ptr(nops, ctypes.c_int32), _ptr(ops, ctypes.c_int32), cnt, ctypes.byref(n)))
+        return coef, cls, nops, ops
+
+    def tree(self):
+        n = ctypes.c_int64()
+        check(lib().qed_model_tree(self._h, None, 0, ctypes.byref(n)))
+        out = np.zeros((n.value, 7), dtype=np.int32)
+        check(lib().qed_model_tree(self._h, _ptr(out, ctypes.c_int32), n.value, ctypes.byref(n)))
+        return out
+
+    def sectors(self, chi):
+        """List over nodes of {q: dim} for the bond above each node."""
+        n = ctypes.c_int64()
+        check(lib().qed_model_sectors(self._h, chi, None, 0, ctypes.byref(n)))
+        out = np.zeros((n.value, 3), dtype=np.int32)
+        check(lib().qed_model_sectors(self._h, chi, _ptr(out, ctypes.c_int32), n.value, ctypes.byref(n)))
+        nn = self.info()["n_nodes"]
+        bonds = [dict() for _ in range(nn)]
+        for node, q, d in out:
+            bonds[int(node)][int(q)] = int(d)
+        return bonds
+
+
+class TTN:
+    """Device-resident TTN state (ttn_create).  ``stream``: an integer
+    cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream) or None."""
+
+    def __init__(self, model, chi, seed=0, precision="fp64", stream=None):
+        self.model = model
+        h = ctypes.c_void_p()
+        check(lib().ttn_create(model.handle, chi, seed, PREC[precision], ctypes.c_void_p(stream or 0),
+                               ctypes.byref(h)))
+        self._h = h
+        self.chi = chi
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().ttn_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def sweep(self, n=1, tol=1e-12, max_krylov=64, allow_noconv=False):
+        st = SweepStats()
+        check(lib().ttn_sweep(self._h, n, tol, max_krylov, ctypes.byref(st)), allow=(-4,) if allow_noconv else ())
+        return dict(energy=st.energy, matvecs=st.matvecs, node_updates=st.node_updates,
+                    not_converged=st.not_converged, max_rel_residual=st.max_rel_residual, seconds=st.seconds)
+
+    def optimize_node(self, node, tol=1e-12, max_krylov=64):
+        e = ctypes.c_double()
+        check(lib().ttn_optimize_node(self._h, node, tol, max_krylov, ctypes.byref(e)))
+        return e.value
+
+    def move_center(self, node):
+        check(lib().ttn_move_center(self._h, node))
+
+    def info(self):
+        c, nn, mx = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        check(lib().ttn_info(self._h, ctypes.byref(c), ctypes.byref(nn), ctypes.byref(mx)))
+        return dict(center=c.value, n_nodes=nn.value, max_node_size=mx.value)
+
+    def node_size(self, node):
+        n = ctypes.c_int64()
+        check(lib().ttn_node_size(self._h, node, ctypes.byref(n)))
+        return n.value
+
+    def energy(self):
+        """(E_total, E_without_penalty, {class: <H_class>})."""
+        et, ew = ctypes.c_double(), ctypes.c_double()
+        parts = np.zeros(5)
+        check(lib().ttn_energy(self._h, ctypes.byref(et), ctypes.byref(ew), _ptr(parts, ctypes.c_double)))
+        return et.value, ew.value, dict(zip(CLASSES, parts.tolist()))
+
+    def measure(self, kind):
+        k = MEAS[kind]
+        n = ctypes.c_int64()
+        check(lib().ttn_measure(self._h, k, None, 0, ctypes.byref(n)))
+        out = np.zeros(n.value)
+        check(lib().ttn_measure(self._h, k, _ptr(out, ctypes.c_double), n.value, ctypes.byref(n)))
+        return out
+
+    def node_export(self, node):
+        n = self.node_size(node)
+        out = np.zeros(n)
+        nn = ctypes.c_int64()
+        check(lib().ttn_node_export(self._h, node, _ptr(out, ctypes.c_double), n, ctypes.byref(nn)))
+        return out
+
+    def node_import(self, node, data):
+        data = np.ascontiguousarray(data, dtype=np.float64)
+        check(lib().ttn_node_import(self._h, node, _ptr(data, ctypes.c_double), data.size))
+
+    def apply_heff(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.zeros_like(x)
+        check(lib().ttn_apply_heff(self._h, _ptr(x, ctypes.c_double), _ptr(y, ctypes.c_double), x.size))
+        return y
+
+    def apply_heff_device(self, x_ptr, y_ptr, n):
+        check(lib().ttn_apply_heff_device(self._h, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), n))

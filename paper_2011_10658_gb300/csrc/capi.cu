@@ -1,0 +1,437 @@
+// C ABI of the qedttn library (see include/qedttn.h for the contract).
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <exception>
+#include <string>
+#include <vector>
+
+#include "../../include/qedttn.h"
+#include "engine.h"
+#include "model.h"
+
+namespace {
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int engine_status(qed::Engine* e, int rc) {
+  if (rc == 0) return QED_OK;
+  g_err = e->error();
+  if (rc == -2) return QED_ENOMEM;
+  if (rc == -5) return QED_ENAN;
+  if (rc == -7) return QED_EUNSUPPORTED;
+  if (rc == -1) return QED_EINVAL;
+  return QED_ECUDA;
+}
+
+bool pow2(int v) { return v >= 1 && (v & (v - 1)) == 0; }
+}  // namespace
+
+struct qed_model {
+  qed::Params p;
+  std::vector<qed::Term> terms;
+  double constant = 0.0;
+  std::vector<qed::TreeNode> nodes;
+};
+
+struct ttn_state {
+  qed::Engine* engine = nullptr;
+  const qed_model* model = nullptr;
+};
+
+#define QED_TRY(...)                                    \
+  try {                                                 \
+    __VA_ARGS__                                         \
+  } catch (const std::bad_alloc&) {                     \
+    return fail(QED_ENOMEM, "out of host memory");      \
+  } catch (const std::exception& ex) {                  \
+    return fail(QED_EINVAL, ex.what());                 \
+  } catch (...) {                                       \
+    return fail(QED_EINVAL, "unknown error");           \
+  }
+
+extern "C" {
+
+#define QED_API __attribute__((visibility("default")))
+
+QED_API const char* qed_last_error(void) { return g_err.c_str(); }
+
+QED_API int qed_basis(int parity, int8_t* table, int32_t* n_rows) {
+  if (parity != 1 && parity != -1) return fail(QED_EINVAL, "parity must be +1 or -1");
+  if (n_rows) *n_rows = qed::kLocalDim;
+  if (!table) return QED_OK;
+  QED_TRY(qed::enumerate_basis(parity, table); return QED_OK;)
+}
+
+QED_API int qed_local_op(int parity, int op_kind, int j1, int j2, int16_t* src, double* val) {
+  if (parity != 1 && parity != -1) return fail(QED_EINVAL, "parity must be +1 or -1");
+  if (!src || !val) return fail(QED_EINVAL, "null output");
+  if (op_kind < QED_OP_IDENTITY || op_kind > QED_OP_E2) return fail(QED_EINVAL, "unknown op kind");
+  if (op_kind != QED_OP_E2 && (j1 < 0 || j1 > 5)) return fail(QED_EINVAL, "half-link index out of range");
+  if (op_kind == QED_OP_C && (j2 < 0 || j2 > 5 || j1 == j2)) return fail(QED_EINVAL, "C needs two distinct half-links");
+  if (op_kind == QED_OP_P && (j2 < 0 || j2 > 2)) return fail(QED_EINVAL, "P needs k in 0..2");
+  if (op_kind == QED_OP_E2 && (j1 < 0 || j1 > 63)) return fail(QED_EINVAL, "E2 mask out of range");
+  QED_TRY(
+    qed::OpKey k;
+    k.kind = op_kind;
+    k.a = j1;
+    k.b = j2;
+    qed::SiteOp op;
+    qed::build_site_op(parity, k, &op);
+    for (int i = 0; i < qed::kLocalDim; ++i) {
+      src[i] = op.src[i];
+      val[i] = op.val[i];
+    }
+    return QED_OK;)
+}
+
+QED_API int qed_model_create(const qed_params* p, qed_model** out) {
+  if (!p || !out) return fail(QED_EINVAL, "null argument");
+  *out = nullptr;
+  if (p->boundary != 0) return fail(QED_EUNSUPPORTED, "only open boundaries (boundary = 0) are built");
+  if (!pow2(p->Lx) || !pow2(p->Ly) || !pow2(p->Lz) || p->Lx * p->Ly * p->Lz < 2 || p->Lx * p->Ly * p->Lz > 4096)
+    return fail(QED_EINVAL, "lattice extents must be powers of two, 2 <= sites <= 4096");
+  const double c[5] = {p->t, p->m, p->ge2, p->cB, p->nu};
+  for (double v : c)
+    if (!std::isfinite(v)) return fail(QED_ENAN, "non-finite coupling");
+  QED_TRY(
+    qed_model* m = new qed_model;
+    m->p.Lx = p->Lx; m->p.Ly = p->Ly; m->p.Lz = p->Lz; m->p.boundary = p->boundary;
+    m->p.t = p->t; m->p.m = p->m; m->p.ge2 = p->ge2; m->p.cB = p->cB; m->p.nu = p->nu; m->p.Q = p->Q;
+    qed::build_terms(m->p, &m->terms, &m->constant);
+    m->nodes = qed::build_tree(p->Lx, p->Ly, p->Lz);
+    *out = m;
+    return QED_OK;)
+}
+
+QED_API void qed_model_destroy(qed_model* m) { delete m; }
+
+QED_API int qed_model_info(const qed_model* m, int32_t* n_sites, int32_t* n_terms, int32_t* n_nodes, double* constant) {
+  if (!m) return fail(QED_EINVAL, "null model");
+  if (n_sites) *n_sites = m->p.Lx * m->p.Ly * m->p.Lz;
+  if (n_terms) *n_terms = (int32_t)m->terms.size();
+  if (n_nodes) *n_nodes = (int32_t)m->nodes.size();
+  if (constant) *constant = m->constant;
+  return QED_OK;
+}
+
+QED_API int qed_model_terms(const qed_model* m, double* coef, int32_t* cls, int32_t* n_ops, int32_t* ops, int64_t cap,
+                    int64_t* n) {
+  if (!m) return fail(QED_EINVAL, "null model");
+  if (n) *n = (int64_t)m->terms.size();
+  if (!coef || cap <= 0) return QED_OK;
+  if (cap < (int64_t)m->terms.size()) return fail(QED_EINVAL, "buffer too small");
+  for (size_t i = 0; i < m->terms.size(); ++i) {
+    const qed::Term& t = m->terms[i];
+    coef[i] = t.coef;
+    if (cls) cls[i] = t.cls;
+    if (n_ops) n_ops[i] = (int32_t)t.ops.size();
+    if (ops)
+      for (size_t f = 0; f < 4; ++f) {
+        int32_t* o = ops + (i * 4 + f) * 4;
+        if (f < t.ops.size()) {
+          o[0] = t.ops[f].first; o[1] = t.ops[f].second.kind; o[2] = t.ops[f].second.a; o[3] = t.ops[f].second.b;
+        } else {
+          o[0] = o[1] = o[2] = o[3] = -1;
+        }
+      }
+  }
+  return QED_OK;
+}
+
+QED_API int qed_model_tree(const qed_model* m, int32_t* nodes, int64_t cap, int64_t* n) {
+  if (!m) return fail(QED_EINVAL, "null model");
+  if (n) *n = (int64_t)m->nodes.size();
+  if (!nodes || cap <= 0) return QED_OK;
+  if (cap < (int64_t)m->nodes.size()) return fail(QED_EINVAL, "buffer too small");
+  for (size_t i = 0; i < m->nodes.size(); ++i) {
+    const qed::TreeNode& t = m->nodes[i];
+    int32_t* o = nodes + 7 * i;
+    o[0] = t.layer; o[1] = t.axis; o[2] = t.child_kind[0]; o[3] = t.child[0];
+    o[4] = t.child_kind[1]; o[5] = t.child[1]; o[6] = t.parent;
+  }
+  return QED_OK;
+}
+
+QED_API int qed_model_sectors(const qed_model* m, int32_t chi, int32_t* triples, int64_t cap, int64_t* n) {
+  if (!m) return fail(QED_EINVAL, "null model");
+  if (chi < 1 || chi > 4096) return fail(QED_EINVAL, "chi out of range");
+  QED_TRY(
+    std::vector<qed::Sectors> bonds;
+    std::string err;
+    if (!qed::sector_table(m->p, chi, m->nodes, &bonds, &err)) return fail(QED_EUNSUPPORTED, err);
+    int64_t total = 0;
+    for (auto& b : bonds) total += (int64_t)b.q.size();
+    if (n) *n = total;
+    if (!triples || cap <= 0) return QED_OK;
+    if (cap < total) return fail(QED_EINVAL, "buffer too small");
+    int64_t k = 0;
+    for (size_t i = 0; i < bonds.size(); ++i)
+      for (size_t j = 0; j < bonds[i].q.size(); ++j) {
+        triples[3 * k] = (int32_t)i;
+        triples[3 * k + 1] = bonds[i].q[j];
+        triples[3 * k + 2] = bonds[i].dim[j];
+        ++k;
+      }
+    return QED_OK;)
+}
+
+QED_API int ttn_create(const qed_model* m, int32_t chi, uint64_t seed, int precision, void* cuda_stream, ttn_state** out) {
+  if (!m || !out) return fail(QED_EINVAL, "null argument");
+  *out = nullptr;
+  if (chi < 1 || chi > 512) return fail(QED_EINVAL, "chi out of range (1..512)");
+  if (precision != QED_PREC_FP64 && precision != QED_PREC_TF32 && precision != QED_PREC_BF16)
+    return fail(QED_EINVAL, "unknown precision");
+  int dev_count = 0;
+  if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0)
+    return fail(QED_ECUDA, "no CUDA device available");
+  QED_TRY(
+    ttn_state* s = new ttn_state;
+    try {
+      s->engine = new qed::Engine(m->p, chi, seed, precision, (cudaStream_t)cuda_stream);
+    } catch (...) {
+      delete s;
+      throw;
+    }
+    s->model = m;
+    *out = s;
+    return QED_OK;)
+}
+
+QED_API void ttn_destroy(ttn_state* s) {
+  if (!s) return;
+  delete s->engine;
+  delete s;
+}
+
+QED_API int ttn_sweep(ttn_state* s, int32_t n_sweeps, double tol, int32_t max_krylov, ttn_sweep_stats* out) {
+  if (!s) return fail(QED_EINVAL, "null state");
+  if (n_sweeps < 0 || !(tol > 0.0) || max_krylov < 2 || max_krylov > 128)
+    return fail(QED_EINVAL, "n_sweeps >= 0, tol > 0, 2 <= max_krylov <= 128");
+  QED_TRY(
+    auto t0 = std::chrono::steady_clock::now();
+    qed::SweepStats st;
+    for (int i = 0; i < n_sweeps; ++i) {
+      int rc = s->engine->sweep(tol, max_krylov, &st, nullptr);
+      if (rc) return engine_status(s->engine, rc);
+    }
+    auto t1 = std::chrono::steady_clock::now();
+    if (out) {
+      out->energy = st.energy;
+      out->matvecs = st.matvecs;
+      out->node_updates = st.node_updates;
+      out->not_converged = st.not_converged;
+      out->max_rel_residual = st.max_residual;
+      out->seconds = std::chrono::duration<double>(t1 - t0).count();
+    }
+    if (st.not_converged) return fail(QED_ENOCONV, "some node updates stopped above tolerance");
+    return QED_OK;)
+}
+
+QED_API int ttn_optimize_node(ttn_state* s, int32_t node, double tol, int32_t max_krylov, double* energy) {
+  if (!s) return fail(QED_EINVAL, "null state");
+  if (node < 0 || node >= s->engine->n_nodes()) return fail(QED_EINVAL, "node out of range");
+  if (!(tol > 0.0) || max_krylov < 2 || max_krylov > 128) return fail(QED_EINVAL, "bad tolerance or Krylov size");
+  QED_TRY(
+    qed::SweepStats st;
+    double e = 0;
+    int rc = s->engine->optimize_node(node, tol, max_krylov, &st, &e);
+    if (rc) return engine_status(s->engine, rc);
+    if (energy) *energy = e;
+    if (st.not_converged) return fail(QED_ENOCONV, "node update stopped above tolerance");
+    return QED_OK;)
+}
+
+QED_API int ttn_move_center(ttn_state* s, int32_t node) {
+  if (!s) return fail(QED_EINVAL, "null state");
+  if (node < 0 || node >= s->engine->n_nodes()) return fail(QED_EINVAL, "node out of range");
+  QED_TRY(return engine_status(s->engine, s->engine->move_to(node));)
+}
+
+QED_API int ttn_info(ttn_state* s, int32_t* center, int32_t* n_nodes, int64_t* max_node_size) {
+  if (!s) return fail(QED_EINVAL, "null state");
+  if (center) *center = s->engine->center();
+  if (n_nodes) *n_nodes = s->engine->n_nodes();
+  if (max_node_size) {
+    int64_t mx = 0;
+    for (int i = 0; i < s->engine->n_nodes(); ++i) mx = std::max<int64_t>(mx, s->engine->node_size(i));
+    *max_node_size = mx;
+  }
+  return QED_OK;
+}
+
+QED_API int ttn_node_size(ttn_state* s, int32_t node, int64_t* n) {
+  if (!s || !n) return fail(QED_EINVAL, "null argument");
+  if (node < 0 || node >= s->engine->n_nodes()) return fail(QED_EINVAL, "node out of range");
+  *n = s->engine->node_size(node);
+  return QED_OK;
+}
+
+QED_API int ttn_energy(ttn_state* s, double* E_total, double* E_without_penalty, double* E_class) {
+  if (!s) return fail(QED_EINVAL, "null state");
+  QED_TRY(
+    double tot = 0, parts[qed::N_CLASSES];
+    int rc = s->engine->energy(&tot, parts);
+    if (rc) return engine_status(s->engine, rc);
+    if (E_total) *E_total = tot;
+    if (E_without_penalty) *E_without_penalty = tot - parts[qed::CLS_NU];
+    if (E_class)
+      for (int c = 0; c < qed::N_CLASSES; ++c) E_class[c] = parts[c];
+    return QED_OK;)
+}
+
+QED_API int ttn_measure(ttn_state* s, int kind, double* out, int64_t cap, int64_t* n) {
+  if (!s) return fail(QED_EINVAL, "null state");
+  const qed::Params& p = s->model->p;
+  qed::Lattice lat{p.Lx, p.Ly, p.Lz};
+  const int N = lat.n_sites();
+  int64_t need = 0;
+  int layers = 0;
+  {
+    const int mn = std::min(p.Lx, std::min(p.Ly, p.Lz));
+    layers = (mn + 1) / 2;
+  }
+  switch (kind) {
+    case QED_MEAS_PROBS: need = (int64_t)N * qed::kLocalDim; break;
+    case QED_MEAS_PHI: case QED_MEAS_NX: case QED_MEAS_QX: need = N; break;
+    case QED_MEAS_K: need = (int64_t)N * 6; break;
+    case QED_MEAS_ELINK: need = lat.n_links(); break;
+    case QED_MEAS_SCALARS: need = 4; break;
+    case QED_MEAS_SIGMA: need = layers; break;
+    default: return fail(QED_EINVAL, "unknown measurement kind");
+  }
+  if (n) *n = need;
+  if (!out || cap <= 0) return QED_OK;
+  if (cap < need) return fail(QED_EINVAL, "buffer too small");
+  QED_TRY(
+    std::vector<double> probs;
+    int rc = s->engine->site_probabilities(&probs);
+    if (rc) return engine_status(s->engine, rc);
+    if (kind == QED_MEAS_PROBS) {
+      std::memcpy(out, probs.data(), need * sizeof(double));
+      return QED_OK;
+    }
+    std::vector<int8_t> tab[2];
+    for (int t = 0; t < 2; ++t) {
+      tab[t].resize(qed::kLocalDim * 9);
+      qed::enumerate_basis(t == 0 ? 1 : -1, tab[t].data());
+    }
+    std::vector<double> phi(N), q(N), k(N * 6);
+    for (int x = 0; x < N; ++x) {
+      const int8_t* tb = tab[lat.parity(x) == 1 ? 0 : 1].data();
+      double a = 0, b = 0, kk[6] = {0, 0, 0, 0, 0, 0};
+      for (int r = 0; r < qed::kLocalDim; ++r) {
+        const double pr = probs[(size_t)x * qed::kLocalDim + r];
+        a += pr * tb[9 * r];
+        b += pr * tb[9 * r + 8];
+        for (int j = 0; j < 6; ++j) kk[j] += pr * tb[9 * r + 1 + j];
+      }
+      phi[x] = a;
+      q[x] = b;
+      for (int j = 0; j < 6; ++j) k[x * 6 + j] = kk[j];
+    }
+    if (kind == QED_MEAS_PHI) { for (int x = 0; x < N; ++x) out[x] = phi[x]; return QED_OK; }
+    if (kind == QED_MEAS_QX) { for (int x = 0; x < N; ++x) out[x] = q[x]; return QED_OK; }
+    if (kind == QED_MEAS_NX) {
+      for (int x = 0; x < N; ++x) { int par = lat.parity(x); out[x] = 0.5 * (1 + par) - par * phi[x]; }
+      return QED_OK;
+    }
+    if (kind == QED_MEAS_K) { for (int i = 0; i < N * 6; ++i) out[i] = k[i]; return QED_OK; }
+    double dL = 0.0;
+    int li = 0;
+    std::vector<double> elink;
+    for (int x = 0; x < N; ++x)
+      for (int mu = 0; mu < 3; ++mu) {
+        int y = lat.neighbour(x, mu, +1);
+        if (y < 0) continue;
+        const double kx = k[x * 6 + 3 + mu], ky = k[y * 6 + mu];
+        elink.push_back(1.0 - kx);
+        dL += std::fabs(kx + ky - 2.0);
+        ++li;
+      }
+    if (kind == QED_MEAS_ELINK) { for (size_t i = 0; i < elink.size(); ++i) out[i] = elink[i]; return QED_OK; }
+    if (kind == QED_MEAS_SCALARS) {
+      double rho = 0, qs = 0;
+      for (int x = 0; x < N; ++x) {
+        int par = lat.parity(x);
+        rho += 0.5 * (1 + par) - par * phi[x];
+        qs += q[x];
+      }
+      out[0] = rho / N;
+      out[1] = dL;
+      out[2] = qs;
+      out[3] = layers;
+      return QED_OK;
+    }
+    // sigma(l): mean <psi^dag psi> over sites at distance l from the closest boundary
+    std::vector<double> sum(layers, 0.0), cnt(layers, 0.0);
+    for (int x = 0; x < N; ++x) {
+      int c[3];
+      lat.coords(x, c);
+      const int dims[3] = {p.Lx, p.Ly, p.Lz};
+      int l = 1 << 30;
+      for (int a = 0; a < 3; ++a) l = std::min(l, std::min(c[a], dims[a] - 1 - c[a]));
+      if (l < layers) { sum[l] += phi[x]; cnt[l] += 1; }
+    }
+    for (int l = 0; l < layers; ++l) out[l] = cnt[l] > 0 ? sum[l] / cnt[l] : 0.0;
+    return QED_OK;)
+}
+
+QED_API int ttn_node_export(ttn_state* s, int32_t node, double* buf, int64_t cap, int64_t* n) {
+  if (!s) return fail(QED_EINVAL, "null state");
+  if (node < 0 || node >= s->engine->n_nodes()) return fail(QED_EINVAL, "node out of range");
+  const int64_t need = s->engine->node_size(node);
+  if (n) *n = need;
+  if (!buf || cap <= 0) return QED_OK;
+  if (cap < need) return fail(QED_EINVAL, "buffer too small");
+  QED_TRY(
+    std::vector<double> h;
+    int rc = s->engine->node_export(node, &h);
+    if (rc) return engine_status(s->engine, rc);
+    std::memcpy(buf, h.data(), need * sizeof(double));
+    return QED_OK;)
+}
+
+QED_API int ttn_node_import(ttn_state* s, int32_t node, const double* buf, int64_t n) {
+  if (!s || !buf) return fail(QED_EINVAL, "null argument");
+  if (node < 0 || node >= s->engine->n_nodes()) return fail(QED_EINVAL, "node out of range");
+  if (n != s->engine->node_size(node)) return fail(QED_EINVAL, "size mismatch");
+  QED_TRY(
+    std::vector<double> h(buf, buf + n);
+    int rc = s->engine->node_import(node, h);
+    if (rc == -5) return fail(QED_ENAN, "non-finite tensor entry");
+    if (rc == -1) return fail(QED_EINVAL, "size mismatch");
+    return engine_status(s->engine, rc);)
+}
+
+QED_API int ttn_apply_heff(ttn_state* s, const double* x, double* y, int64_t n) {
+  if (!s || !x || !y) return fail(QED_EINVAL, "null argument");
+  const int64_t need = s->engine->node_size(s->engine->center());
+  if (n != need) return fail(QED_EINVAL, "size must equal the centre tensor size");
+  QED_TRY(
+    double *dx = nullptr, *dy = nullptr;
+    if (cudaMalloc(&dx, n * sizeof(double)) != cudaSuccess) return fail(QED_ENOMEM, "device allocation");
+    if (cudaMalloc(&dy, n * sizeof(double)) != cudaSuccess) { cudaFree(dx); return fail(QED_ENOMEM, "device allocation"); }
+    cudaStream_t st = s->engine->stream();
+    cudaMemcpyAsync(dx, x, n * sizeof(double), cudaMemcpyHostToDevice, st);
+    int rc = s->engine->apply_heff(dx, dy, -1);
+    if (!rc) cudaMemcpyAsync(y, dy, n * sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaFree(dx);
+    cudaFree(dy);
+    if (rc) return engine_status(s->engine, rc);
+    if (e != cudaSuccess) return fail(QED_ECUDA, cudaGetErrorString(e));
+    return QED_OK;)
+}
+
+QED_API int ttn_apply_heff_device(ttn_state* s, const double* x_device, double* y_device, int64_t n) {
+  if (!s || !x_device || !y_device) return fail(QED_EINVAL, "null argument");
+  if (n != s->engine->node_size(s->engine->center())) return fail(QED_EINVAL, "size must equal the centre tensor size");
+  QED_TRY(return engine_status(s->engine, s->engine->apply_heff(x_device, y_device, -1));)
+}
+
+}  // extern "C"

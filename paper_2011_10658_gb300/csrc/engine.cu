@@ -1,0 +1,1605 @@
+// TTN sweep engine (host orchestration of the device kernels).
+//
+// Method (Methods, "Tensor Networks"): single-tensor optimisation with
+// (i) H_eff from the Hamiltonian contracted with all other tensors,
+// (ii) its lowest eigenpair by a Krylov method, (iii) the tensor replaced by
+// the eigenvector, sweeping from the lowest to the highest layer.  Global
+// U(1) charge conservation is built into the block structure of every
+// tensor.  All other tensors are kept isometric towards the centre; a move
+// of the centre is a per-sector QR (CholeskyQR2 here) whose R factor is
+// absorbed by the neighbour.
+#include "engine.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <stdexcept>
+
+namespace qed {
+
+namespace {
+constexpr long long kKPart = 4096;     // split-K granularity for tall contractions
+constexpr int kMaxKrylov = 128;
+// Centre-move QR rank handling: a sector whose QR diagonal falls below
+// kQrFallback x (largest column norm) is factorised by Gram-Schmidt, where a
+// remainder below kQrDependent x (largest column norm) marks a dependent
+// column completed by the first unit vector with remainder above kQrAccept.
+constexpr double kQrFallback = 1e-6;
+constexpr double kQrDependent = 1e-9;
+constexpr double kQrAccept = 0.5;
+constexpr long long kZPoolBudget = 64LL << 20;   // doubles in the Z work pool for operator updates
+}  // namespace
+
+// ------------------------------------------------------------------ Layout
+void Layout::build(const Sectors& a, const Sectors& b, const Sectors& c, int shift_) {
+  leg[0] = a;
+  leg[1] = b;
+  leg[2] = c;
+  shift = shift_;
+  blk.clear();
+  index.clear();
+  sec_off.assign(c.q.size(), 0);
+  sec_rows.assign(c.q.size(), 0);
+  long long off = 0;
+  for (size_t ic = 0; ic < c.q.size(); ++ic) {
+    sec_off[ic] = off;
+    int rows = 0;
+    for (size_t ia = 0; ia < a.q.size(); ++ia) {
+      int qb = c.q[ic] + shift - a.q[ia];
+      int ib = b.find(qb);
+      if (ib < 0) continue;
+      Blk k;
+      k.ia = (int)ia;
+      k.ib = ib;
+      k.ic = (int)ic;
+      k.da = a.dim[ia];
+      k.db = b.dim[ib];
+      k.dc = c.dim[ic];
+      k.off = off;
+      k.row0 = rows;
+      index[{k.ia, k.ib}] = (int)blk.size();
+      blk.push_back(k);
+      off += (long long)k.da * k.db * k.dc;
+      rows += k.da * k.db;
+    }
+    sec_rows[ic] = rows;
+  }
+  size = off;
+}
+
+// ------------------------------------------------------------------ KPlan
+int KPlan::add_output(double* C, long long c_m, long long c_n, int M, int N, int accumulate) {
+  auto key = std::make_tuple((uintptr_t)C, c_m, c_n, M, N);
+  auto it = out_index.find(key);
+  if (it != out_index.end()) {
+    current = it->second;
+    return current;
+  }
+  KOutput o;
+  o.C = C;
+  o.c_m = c_m;
+  o.c_n = c_n;
+  o.M = M;
+  o.N = N;
+  o.chunk_begin = 0;
+  o.chunk_end = 0;
+  o.accumulate = accumulate;
+  o.n_parts = 1;
+  o.part_off = 0;
+  outs.push_back(o);
+  out_chunks.emplace_back();
+  current = (int)outs.size() - 1;
+  out_index[key] = current;
+  return current;
+}
+
+void KPlan::add_chunk(const KChunk& c) { out_chunks[current].push_back(c); }
+
+// Tiles of 32 x 32 per output.  Outputs with few tiles and long K are split
+// into parts (sub-ranges of K, chunks cut where needed) whose partial sums
+// go to scratch and are reduced in a fixed order afterwards.
+void KPlan::finalize(long long k_part) {
+  // flatten the per-output chunk lists (idempotent if already flat)
+  if (!out_chunks.empty()) {
+    chunks.clear();
+    for (size_t oi = 0; oi < outs.size(); ++oi) {
+      outs[oi].chunk_begin = (int)chunks.size();
+      chunks.insert(chunks.end(), out_chunks[oi].begin(), out_chunks[oi].end());
+      outs[oi].chunk_end = (int)chunks.size();
+    }
+    out_chunks.clear();
+    out_index.clear();
+  }
+  std::vector<KChunk> nc;
+  nc.reserve(chunks.size());
+  tiles.clear();
+  red.clear();
+  scratch_need = 0;
+  for (size_t oi = 0; oi < outs.size(); ++oi) {
+    KOutput& o = outs[oi];
+    const int tm = (o.M + KT_BM - 1) / KT_BM, tn = (o.N + KT_BN - 1) / KT_BN;
+    long long ktot = 0;
+    for (int c = o.chunk_begin; c < o.chunk_end; ++c) ktot += chunks[c].add ? 1 : chunks[c].K;
+    const bool split = ktot > 2 * k_part && tm * tn <= 8;
+    std::vector<std::pair<int, int>> parts;   // ranges in nc
+    const int begin = (int)nc.size();
+    if (!split) {
+      for (int c = o.chunk_begin; c < o.chunk_end; ++c) nc.push_back(chunks[c]);
+      parts.push_back({begin, (int)nc.size()});
+    } else {
+      long long acc = 0;
+      int part_begin = begin;
+      for (int c = o.chunk_begin; c < o.chunk_end; ++c) {
+        const KChunk& ch = chunks[c];
+        if (ch.add) {
+          nc.push_back(ch);
+          acc += 1;
+        } else {
+          for (int k0 = 0; k0 < ch.K; k0 += (int)k_part) {
+            KChunk s = ch;
+            s.K = std::min<int>((int)k_part, ch.K - k0);
+            if (ch.bmap) {
+              s.bmap = ch.bmap + k0;
+              if (ch.bval) s.bval = ch.bval + k0;
+            } else {
+              s.B = ch.B + (long long)k0 * ch.b_k;
+            }
+            s.A = ch.A + (long long)k0 * ch.a_k;
+            nc.push_back(s);
+            acc += s.K;
+            if (acc >= k_part) {
+              parts.push_back({part_begin, (int)nc.size()});
+              part_begin = (int)nc.size();
+              acc = 0;
+            }
+          }
+        }
+      }
+      if ((int)nc.size() > part_begin) parts.push_back({part_begin, (int)nc.size()});
+    }
+    o.chunk_begin = begin;
+    o.chunk_end = (int)nc.size();
+    if (parts.size() > 1) {
+      o.n_parts = (int)parts.size();
+      o.part_off = scratch_need;
+      scratch_need += (long long)o.n_parts * o.M * o.N;
+      red.push_back((int)oi);
+    } else {
+      o.n_parts = 1;
+    }
+    for (size_t pi = 0; pi < parts.size(); ++pi)
+      for (int i = 0; i < tm; ++i)
+        for (int j = 0; j < tn; ++j) {
+          KTile t;
+          t.out = (int)oi;
+          t.m0 = i * KT_BM;
+          t.n0 = j * KT_BN;
+          t.chunk_begin = parts[pi].first;
+          t.chunk_end = parts[pi].second;
+          t.part = parts.size() > 1 ? (int)pi : -1;
+          tiles.push_back(t);
+        }
+  }
+  chunks.swap(nc);
+}
+
+template <typename T>
+static void grow_upload(T*& dptr, size_t& cap, const std::vector<T>& host, cudaStream_t s) {
+  if (host.empty()) return;
+  if (host.size() > cap) {
+    if (dptr) cudaFree(dptr);
+    cap = host.size() + host.size() / 2 + 16;
+    cudaMalloc(&dptr, cap * sizeof(T));
+  }
+  cudaMemcpyAsync(dptr, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+}
+
+void KPlan::upload(cudaStream_t s) {
+  grow_upload(d_chunks, cap_chunks, chunks, s);
+  grow_upload(d_outs, cap_outs, outs, s);
+  grow_upload(d_tiles, cap_tiles, tiles, s);
+  grow_upload(d_red, cap_red, red, s);
+}
+
+void KPlan::release() {
+  if (d_chunks) cudaFree(d_chunks);
+  if (d_outs) cudaFree(d_outs);
+  if (d_tiles) cudaFree(d_tiles);
+  if (d_red) cudaFree(d_red);
+  d_chunks = nullptr;
+  d_outs = nullptr;
+  d_tiles = nullptr;
+  d_red = nullptr;
+  cap_chunks = cap_outs = cap_tiles = cap_red = 0;
+}
+
+static KChunk make_chunk() {
+  KChunk c;
+  std::memset(&c, 0, sizeof(c));
+  c.alpha = 1.0;
+  return c;
+}
+
+// ------------------------------------------------------------------ Engine
+void* Engine::dalloc(size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) throw std::runtime_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  allocs_.push_back(p);
+  bytes_ += (long long)bytes;
+  track(p, bytes);
+  return p;
+}
+
+bool Engine::check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return true;
+  err_ = std::string(what) + ": " + cudaGetErrorString(e);
+  return false;
+}
+
+const SiteOp* Engine::site_op(int parity, const OpKey& key) {
+  const long long packed = (((long long)(parity + 1) * 16 + key.kind) * 1024 + key.a) * 1024 + key.b;
+  auto it = site_ops_.find(packed);
+  if (it != site_ops_.end()) return it->second;
+  SiteOp* op = new SiteOp;
+  build_site_op(parity, key, op);
+  site_ops_[packed] = op;
+  return op;
+}
+
+bool Engine::touches_sites(int term, const std::vector<char>& reg) const {
+  for (auto& so : terms_[term].ops)
+    if (reg[so.first]) return true;
+  return false;
+}
+
+bool Engine::touches(int term, int node) const { return touches_sites(term, in_region_[node]); }
+
+bool Engine::inside(int term, int node) const {
+  for (auto& so : terms_[term].ops)
+    if (!in_region_[node][so.first]) return false;
+  return true;
+}
+
+bool Engine::crosses(int term, int node) const { return touches(term, node) && !inside(term, node); }
+
+int Engine::leg_node(int node, int leg) const {
+  const TreeNode& nd = nodes_[node];
+  if (leg == 2) return nd.parent;
+  return nd.child_kind[leg] == 1 ? nd.child[leg] : -1;
+}
+
+int Engine::leg_site(int node, int leg) const {
+  const TreeNode& nd = nodes_[node];
+  return (leg < 2 && nd.child_kind[leg] == 0) ? nd.child[leg] : -1;
+}
+
+const Sectors& Engine::leg_sectors(int node, int leg) const { return layout_[node].leg[leg]; }
+
+Layout Engine::shifted(int node, int shift) const {
+  Layout L;
+  L.build(layout_[node].leg[0], layout_[node].leg[1], layout_[node].leg[2], shift);
+  return L;
+}
+
+void Engine::ensure_scratch(long long elems) {
+  if (elems <= scratch_elems_) return;
+  if (scratch_) { untrack(scratch_); cudaFree(scratch_); }
+  scratch_elems_ = elems + elems / 2;
+  cudaMalloc(&scratch_, scratch_elems_ * sizeof(double));
+  track(scratch_, scratch_elems_ * sizeof(double));
+}
+
+void Engine::ensure_zpool(long long elems) {
+  if (elems <= zpool_elems_) return;
+  if (zpool_) { untrack(zpool_); cudaFree(zpool_); }
+  zpool_elems_ = elems + elems / 4;
+  cudaMalloc(&zpool_, zpool_elems_ * sizeof(double));
+  track(zpool_, zpool_elems_ * sizeof(double));
+}
+
+// [p + lo_bytes, p + hi_bytes) inside one tracked allocation?
+bool Engine::in_range(const void* p, long long lo_bytes, long long hi_bytes) const {
+  const uintptr_t a = (uintptr_t)p;
+  auto it = ranges_.upper_bound(a + (lo_bytes < 0 ? 0 : 0));
+  if (it == ranges_.begin()) return false;
+  --it;
+  const long long base = (long long)it->first, size = (long long)it->second;
+  const long long lo = (long long)a + lo_bytes, hi = (long long)a + hi_bytes;
+  return lo >= base && hi <= base + size;
+}
+
+// Host-side check that every chunk and output of a plan stays inside a
+// known device allocation (enabled by QED_VALIDATE=1).  Row-mapped operands
+// are checked over their whole source sector by the row-map builder.
+bool Engine::validate_plan(const KPlan& pl, const char* what) {
+  for (const KOutput& o : pl.outs) {
+    const long long hi = (long long)(o.M - 1) * o.c_m + (long long)(o.N - 1) * o.c_n;
+    if (o.M <= 0 || o.N <= 0 || !in_range(o.C, 0, hi * 8 + 8)) {
+      err_ = std::string(what) + ": output out of range";
+      return false;
+    }
+    for (int ci = o.chunk_begin; ci < o.chunk_end; ++ci) {
+      const KChunk& c = pl.chunks[ci];
+      const int K = c.add ? o.N : c.K;
+      if (K <= 0) { err_ = std::string(what) + ": empty chunk"; return false; }
+      if (!c.amap) {
+        const long long ahi = (long long)(o.M - 1) * c.a_m + (long long)(K - 1) * c.a_k;
+        if (!in_range(c.A, 0, ahi * 8 + 8)) {
+          err_ = std::string(what) + ": A operand out of range";
+          return false;
+        }
+      } else if (!in_range(c.amap, 0, (long long)o.M * 4) || (c.aval && !in_range(c.aval, 0, (long long)o.M * 8))) {
+        err_ = std::string(what) + ": A row map out of range";
+        return false;
+      }
+      if (!c.add) {
+        if (!c.bmap) {
+          const long long bhi = (long long)(K - 1) * c.b_k + (long long)(o.N - 1) * c.b_n;
+          if (!in_range(c.B, 0, bhi * 8 + 8)) {
+            err_ = std::string(what) + ": B operand out of range";
+            return false;
+          }
+        } else if (!in_range(c.bmap, 0, (long long)K * 4) || (c.bval && !in_range(c.bval, 0, (long long)K * 8))) {
+          err_ = std::string(what) + ": B row map out of range";
+          return false;
+        }
+      }
+    }
+  }
+  for (const KTile& t : pl.tiles) {
+    if (t.out < 0 || t.out >= (int)pl.outs.size() || t.chunk_begin < 0 || t.chunk_end > (int)pl.chunks.size()) {
+      err_ = std::string(what) + ": bad tile";
+      return false;
+    }
+    if (t.part >= 0 && !in_range(scratch_, pl.outs[t.out].part_off * 8,
+                                 (pl.outs[t.out].part_off + (long long)(t.part + 1) * pl.outs[t.out].M * pl.outs[t.out].N) * 8)) {
+      err_ = std::string(what) + ": scratch out of range";
+      return false;
+    }
+  }
+  return true;
+}
+
+int Engine::run_plan(KPlan& pl) {
+  pl.finalize(kKPart);
+  ensure_scratch(std::max<long long>(pl.scratch_need, 1));
+  if (validate_ && !validate_plan(pl, "plan")) return -1;
+  pl.upload(stream_);
+  launch_kc_gemm(pl.d_tiles, (int)pl.tiles.size(), pl.d_outs, pl.d_chunks, scratch_, stream_);
+  launch_kc_reduce(pl.d_outs, (int)pl.outs.size(), pl.d_red, (int)pl.red.size(), scratch_, stream_);
+  return check(cudaGetLastError(), "kc_gemm launch") ? 0 : -3;
+}
+
+Engine::Engine(const Params& p, int chi, uint64_t seed, int precision, cudaStream_t stream)
+    : p_(p), chi_(chi), seed_(seed), precision_(precision), stream_(stream) {
+  lat_ = Lattice{p.Lx, p.Ly, p.Lz};
+  const char* v = std::getenv("QED_VALIDATE");
+  validate_ = v && v[0] == '1';
+  build_terms(p, &terms_, &constant_);
+  nodes_ = build_tree(p.Lx, p.Ly, p.Lz);
+  std::string err;
+  if (!sector_table(p, chi, nodes_, &bonds_, &err)) throw std::runtime_error(err);
+  const int n = (int)nodes_.size();
+  in_region_.assign(n, std::vector<char>(lat_.n_sites(), 0));
+  layout_.resize(n);
+  for (const TreeNode& nd : nodes_) {
+    for (int s : nd.sites) in_region_[nd.index][s] = 1;
+    Sectors legs[2];
+    for (int c = 0; c < 2; ++c)
+      legs[c] = nd.child_kind[c] == 0 ? physical_sectors(lat_.parity(nd.child[c])) : bonds_[nd.child[c]];
+    layout_[nd.index].build(legs[0], legs[1], bonds_[nd.index], 0);
+  }
+  T_.assign(n, nullptr);
+  for (int i = 0; i < n; ++i) {
+    T_[i] = (double*)dalloc(layout_[i].size * sizeof(double));
+    nmax_ = std::max(nmax_, layout_[i].size);
+  }
+  up_.resize(n);
+  down_.resize(n);
+  x_in_ = (double*)dalloc(nmax_ * sizeof(double));
+  y_out_ = (double*)dalloc(nmax_ * sizeof(double));
+  tmp_ = (double*)dalloc(nmax_ * sizeof(double));
+  d_scal_ = (double*)dalloc(8192 * sizeof(double));
+  d_partial_ = (double*)dalloc(304 * (kMaxKrylov + 2) * sizeof(double));
+  init_tensors();
+}
+
+Engine::~Engine() {
+  cudaStreamSynchronize(stream_);
+  for (auto& kv : site_ops_) delete kv.second;
+  for (int i = 0; i < 3; ++i) heff_stage_[i].release();
+  work_.release();
+  if (scratch_) cudaFree(scratch_);
+  if (zpool_) cudaFree(zpool_);
+  if (V_) cudaFree(V_);
+  for (void* p : allocs_) cudaFree(p);
+}
+
+// SplitMix64 fill in node order, then per parent sector QR (isometry towards
+// the parent; the R factor is discarded), then the renormalized operators of
+// every bond, bottom-up.  The centre starts at the root.
+void Engine::init_tensors() {
+  uint64_t pos = 0;
+  for (const TreeNode& nd : nodes_) {
+    launch_fill_uniform(T_[nd.index], layout_[nd.index].size, seed_, pos, stream_);
+    pos += (uint64_t)layout_[nd.index].size;
+  }
+  for (const TreeNode& nd : nodes_) {
+    if (qr_toward(nd.index, 2, nullptr) != 0) throw std::runtime_error("initial QR: " + err_);
+  }
+  for (const TreeNode& nd : nodes_)
+    if (nd.parent >= 0 && compute_up(nd.index) != 0) throw std::runtime_error("initial operators: " + err_);
+  center_ = (int)nodes_.size() - 1;
+  if (!check(cudaStreamSynchronize(stream_), "init")) throw std::runtime_error(err_);
+}
+
+// ------------------------------------------------------------------ row maps
+RowMap Engine::build_rowmap_sector(int node, const SiteOp* A, const SiteOp* B, int oc,
+                                   const std::vector<double>* unused) {
+  (void)unused;
+  const Layout& L = layout_[node];
+  const int sl = leg_site(node, 0), sr = leg_site(node, 1);
+  const int pl = lat_.parity(sl), pr = lat_.parity(sr);
+  RowMap rm;
+  const int rows = L.sec_rows[oc];
+  std::vector<int> map(rows, -1);
+  std::vector<double> val(rows, 0.0);
+  bool need_val = false;
+  int src_sec = -1;
+  for (const Layout::Blk& b : L.blk) {
+    if (b.ic != oc) continue;
+    const int a_off = L.leg[0].offset(b.ia), b_off = L.leg[1].offset(b.ib);
+    for (int a = 0; a < b.da; ++a)
+      for (int c = 0; c < b.db; ++c) {
+        const int row = b.row0 + a * b.db + c;
+        const int ag = a_off + a, bg = b_off + c;
+        const int sa = A ? A->src[ag] : ag;
+        const int sb = B ? B->src[bg] : bg;
+        if (sa < 0 || sb < 0) continue;
+        const double v = (A ? A->val[ag] : 1.0) * (B ? B->val[bg] : 1.0);
+        if (v == 0.0) continue;
+        const int ia2 = L.leg[0].find(site_charge(pl, sa));
+        const int ib2 = L.leg[1].find(site_charge(pr, sb));
+        const int k = L.find(ia2, ib2);
+        if (k < 0) continue;   // source label outside the bond sectors: zero
+        const Layout::Blk& sbk = L.blk[k];
+        if (src_sec >= 0 && src_sec != sbk.ic) throw std::logic_error("row map spans two sectors");
+        src_sec = sbk.ic;
+        const int srow = sbk.row0 + (sa - L.leg[0].offset(ia2)) * sbk.db + (sb - L.leg[1].offset(ib2));
+        map[row] = (srow << 1) | (v < 0 ? 1 : 0);
+        val[row] = v;
+        if (std::fabs(v) != 1.0) need_val = true;
+      }
+  }
+  rm.src_sector = src_sec;
+  if (src_sec < 0) return rm;
+  if (need_val) {
+    for (int r = 0; r < rows; ++r)
+      if (map[r] >= 0) map[r] &= ~1;   // sign carried by val
+  }
+  rm.map = (int*)dalloc(std::max(rows, 1) * sizeof(int));
+  cudaMemcpyAsync(rm.map, map.data(), rows * sizeof(int), cudaMemcpyHostToDevice, stream_);
+  if (need_val) {
+    rm.val = (double*)dalloc(std::max(rows, 1) * sizeof(double));
+    cudaMemcpyAsync(rm.val, val.data(), rows * sizeof(double), cudaMemcpyHostToDevice, stream_);
+  }
+  cudaStreamSynchronize(stream_);
+  return rm;
+}
+
+const std::vector<RowMap>& Engine::rowmap(int node, int term) {
+  auto key = std::make_pair(node, term);
+  auto it = rowmaps_.find(key);
+  if (it != rowmaps_.end()) return it->second;
+  const int sl = leg_site(node, 0), sr = leg_site(node, 1);
+  const SiteOp* A = nullptr;
+  const SiteOp* B = nullptr;
+  for (auto& so : terms_[term].ops) {
+    if (so.first == sl) A = site_op(lat_.parity(sl), so.second);
+    if (so.first == sr) B = site_op(lat_.parity(sr), so.second);
+  }
+  std::vector<RowMap> maps;
+  for (size_t oc = 0; oc < layout_[node].leg[2].q.size(); ++oc)
+    maps.push_back(build_rowmap_sector(node, A, B, (int)oc, nullptr));
+  return rowmaps_[key] = maps;
+}
+
+// Diagonal site Hamiltonian (single-site terms, one class or all) on a leg.
+const std::vector<RowMap>& Engine::site_ham_map(int node, int leg, int cls) {
+  auto key = std::make_pair(node, -1000 - 10 * leg - (cls + 1));
+  auto it = rowmaps_.find(key);
+  if (it != rowmaps_.end()) return it->second;
+  const int s = leg_site(node, leg);
+  SiteOp diag;
+  for (int r = 0; r < kLocalDim; ++r) { diag.src[r] = (int16_t)r; diag.val[r] = 0.0; }
+  diag.dq = 0;
+  for (const Term& t : terms_) {
+    if (t.ops.size() != 1 || t.ops[0].first != s) continue;
+    if (cls >= 0 && t.cls != cls) continue;
+    const SiteOp* op = site_op(lat_.parity(s), t.ops[0].second);
+    for (int r = 0; r < kLocalDim; ++r)
+      if (op->src[r] == r) diag.val[r] += t.coef * op->val[r];
+  }
+  std::vector<RowMap> maps;
+  for (size_t oc = 0; oc < layout_[node].leg[2].q.size(); ++oc)
+    maps.push_back(build_rowmap_sector(node, leg == 0 ? &diag : nullptr, leg == 1 ? &diag : nullptr, (int)oc,
+                                       nullptr));
+  return rowmaps_[key] = maps;
+}
+
+// ------------------------------------------------------------------ plans
+// Y = op (x)_leg X.  op[i', i] at P (row-major dimP; transposed: P[i*dimP+i']).
+// Y must be zeroed by the caller where no block of X maps.
+void Engine::plan_leg_apply(KPlan& pl, const Layout& LX, const double* X, const Layout& LY, double* Y, int leg,
+                            const double* P, int dimP, int shiftP, bool transposed, double alpha) {
+  const Sectors& S = LX.leg[leg];
+  for (const Layout::Blk& b : LX.blk) {
+    int ia = b.ia, ib = b.ib;
+    int ic2 = b.ic;
+    int src_idx = leg == 0 ? b.ia : (leg == 1 ? b.ib : b.ic);
+    int dst_idx = S.find(S.q[src_idx] + shiftP);
+    if (dst_idx < 0) continue;
+    if (leg == 0) ia = dst_idx;
+    if (leg == 1) ib = dst_idx;
+    if (leg == 2) ic2 = dst_idx;
+    const int k = LY.find(ia, ib);
+    if (k < 0) continue;
+    const Layout::Blk& yb = LY.blk[k];
+    if (yb.ic != ic2) continue;
+    const long long prow = S.offset(dst_idx), pcol = S.offset(src_idx);
+    // op block element (i' in dst, i in src)
+    const double* Pblk = transposed ? P + pcol * dimP + prow : P + prow * dimP + pcol;
+    const long long p_r = transposed ? 1 : dimP, p_c = transposed ? dimP : 1;
+    if (leg == 0) {
+      pl.add_output(Y + yb.off, (long long)yb.db * yb.dc, 1, yb.da, yb.db * yb.dc, 0);
+      KChunk c = make_chunk();
+      c.A = Pblk; c.a_m = p_r; c.a_k = p_c;
+      c.B = X + b.off; c.b_k = (long long)b.db * b.dc; c.b_n = 1;
+      c.K = b.da; c.alpha = alpha;
+      pl.add_chunk(c);
+    } else if (leg == 1) {
+      for (int a = 0; a < b.da; ++a) {
+        pl.add_output(Y + yb.off + (long long)a * yb.db * yb.dc, yb.dc, 1, yb.db, yb.dc, 0);
+        KChunk c = make_chunk();
+        c.A = Pblk; c.a_m = p_r; c.a_k = p_c;
+        c.B = X + b.off + (long long)a * b.db * b.dc; c.b_k = b.dc; c.b_n = 1;
+        c.K = b.db; c.alpha = alpha;
+        pl.add_chunk(c);
+      }
+    } else {
+      pl.add_output(Y + yb.off, yb.dc, 1, yb.da * yb.db, yb.dc, 0);
+      KChunk c = make_chunk();
+      c.A = X + b.off; c.a_m = b.dc; c.a_k = 1;
+      // B[k, n] = op[n, k]
+      c.B = Pblk; c.b_k = p_c; c.b_n = p_r;
+      c.K = b.dc; c.alpha = alpha;
+      pl.add_chunk(c);
+    }
+  }
+}
+
+// O[i', i] (dimO x dimO, accumulated) += alpha * sum over the other two legs
+// of T[.., i', ..] Z[.., i, ..], T in layout LT (shift 0), Z in LZ.
+// Each output block is one output; contributions are chunks.
+void Engine::plan_contract_but(KPlan& pl, const Layout& LT, const double* T, const Layout& LZ, const double* Z,
+                               int leg, double* O, int dimO, double alpha) {
+  const Sectors& S = LT.leg[leg];
+  std::map<std::pair<int, int>, std::vector<KChunk>> acc;   // (i'-sector, i-sector) -> chunks
+  if (leg == 2) {
+    for (size_t ic1 = 0; ic1 < LT.sec_rows.size(); ++ic1) {
+      const int rows = LT.sec_rows[ic1];
+      if (rows == 0) continue;
+      // Z rows with the same (a, b) blocks have label q' - shift
+      const int ic = S.find(S.q[ic1] - LZ.shift);
+      if (ic < 0 || LZ.sec_rows[ic] != rows) continue;
+      KChunk c = make_chunk();
+      c.A = T + LT.sec_off[ic1]; c.a_m = 1; c.a_k = S.dim[ic1];
+      c.B = Z + LZ.sec_off[ic]; c.b_k = S.dim[ic]; c.b_n = 1;
+      c.K = rows; c.alpha = alpha;
+      acc[{(int)ic1, ic}].push_back(c);
+    }
+  } else {
+    for (const Layout::Blk& tb : LT.blk) {
+      // Z block with the same other-leg indices; this leg shifted by +LZ.shift
+      int ia = tb.ia, ib = tb.ib;
+      int idx = leg == 0 ? tb.ia : tb.ib;
+      int zidx = S.find(S.q[idx] + LZ.shift);
+      if (zidx < 0) continue;
+      if (leg == 0) ia = zidx; else ib = zidx;
+      const int k = LZ.find(ia, ib);
+      if (k < 0) continue;
+      const Layout::Blk& zb = LZ.blk[k];
+      if (zb.ic != tb.ic) continue;
+      if (leg == 0) {
+        KChunk c = make_chunk();
+        c.A = T + tb.off; c.a_m = (long long)tb.db * tb.dc; c.a_k = 1;
+        c.B = Z + zb.off; c.b_k = 1; c.b_n = (long long)zb.db * zb.dc;
+        c.K = tb.db * tb.dc; c.alpha = alpha;
+        acc[{tb.ia, zb.ia}].push_back(c);
+      } else {
+        for (int a = 0; a < tb.da; ++a) {
+          KChunk c = make_chunk();
+          c.A = T + tb.off + (long long)a * tb.db * tb.dc; c.a_m = tb.dc; c.a_k = 1;
+          c.B = Z + zb.off + (long long)a * zb.db * zb.dc; c.b_k = 1; c.b_n = zb.dc;
+          c.K = tb.dc; c.alpha = alpha;
+          acc[{tb.ib, zb.ib}].push_back(c);
+        }
+      }
+    }
+  }
+  for (auto& kv : acc) {
+    const int i1 = kv.first.first, i0 = kv.first.second;
+    pl.add_output(O + S.offset(i1) * dimO + S.offset(i0), dimO, 1, S.dim[i1], S.dim[i0], 1);
+    for (const KChunk& c : kv.second) pl.add_chunk(c);
+  }
+}
+
+// ------------------------------------------------------------------ QR
+// CholeskyQR2 of T[node] with `leg` as the column index, per sector of that
+// leg.  T <- Q.  If Rout != nullptr, R (dim x dim, block diagonal) is written.
+int Engine::qr_toward(int node, int leg, double* Rout) {
+  const Layout& L = layout_[node];
+  const Sectors& S = L.leg[leg];
+  const int dim = S.total();
+  const long long dd = (long long)dim * dim;
+  double* Gb = nullptr;
+  double* Rinv = nullptr;
+  double* Racc = nullptr;
+  double* Rtmp = nullptr;
+  cudaMalloc(&Gb, dd * sizeof(double));
+  cudaMalloc(&Rinv, dd * sizeof(double));
+  cudaMalloc(&Racc, dd * sizeof(double));
+  cudaMalloc(&Rtmp, dd * sizeof(double));
+  track(Gb, dd * sizeof(double));
+  track(Rinv, dd * sizeof(double));
+  track(Racc, dd * sizeof(double));
+  track(Rtmp, dd * sizeof(double));
+  std::vector<long long> off;
+  std::vector<int> nn, ld;
+  int max_n = 0;
+  for (size_t i = 0; i < S.q.size(); ++i) {
+    off.push_back(S.offset((int)i) * dim + S.offset((int)i));
+    nn.push_back(S.dim[i]);
+    ld.push_back(dim);
+    max_n = std::max(max_n, S.dim[i]);
+  }
+  if (max_n > 160) {
+    err_ = "sector dimension above 160 is not supported by the QR kernel";
+    return -7;
+  }
+  long long* d_off = nullptr;
+  int *d_n = nullptr, *d_ld = nullptr, *d_status = nullptr;
+  cudaMalloc(&d_off, off.size() * sizeof(long long));
+  cudaMalloc(&d_n, nn.size() * sizeof(int));
+  cudaMalloc(&d_ld, ld.size() * sizeof(int));
+  cudaMalloc(&d_status, nn.size() * sizeof(int));
+  cudaMemcpyAsync(d_off, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice, stream_);
+  cudaMemcpyAsync(d_n, nn.data(), nn.size() * sizeof(int), cudaMemcpyHostToDevice, stream_);
+  cudaMemcpyAsync(d_ld, ld.data(), ld.size() * sizeof(int), cudaMemcpyHostToDevice, stream_);
+  int rc = 0;
+  bool fallback = false;
+  for (int pass = 0; pass < 2 && rc == 0; ++pass) {
+    cudaMemsetAsync(Gb, 0, dd * sizeof(double), stream_);
+    work_.clear();
+    plan_contract_but(work_, L, T_[node], L, T_[node], leg, Gb, dim, 1.0);
+    rc = run_plan(work_);
+    if (rc) break;
+    cudaMemsetAsync(Rinv, 0, dd * sizeof(double), stream_);
+    launch_cholesky_inv(Gb, Rinv, d_off, d_n, d_ld, (int)nn.size(), max_n, kQrFallback * kQrFallback, d_status,
+                        stream_);
+    std::vector<int> status(nn.size());
+    cudaMemcpyAsync(status.data(), d_status, nn.size() * sizeof(int), cudaMemcpyDeviceToHost, stream_);
+    if (!check(cudaStreamSynchronize(stream_), "cholesky")) { rc = -3; break; }
+    for (int st : status)
+      if (st) fallback = true;
+    if (fallback) {
+      if (pass == 0) break;
+      // second pass of a well-conditioned first pass cannot be ill-conditioned
+      err_ = "CholeskyQR: second pass lost positive definiteness";
+      rc = -5;
+      break;
+    }
+    // T <- T (x)_leg Rinv^T  (Q = X R^{-1})
+    cudaMemsetAsync(tmp_, 0, L.size * sizeof(double), stream_);
+    work_.clear();
+    plan_leg_apply(work_, L, T_[node], L, tmp_, leg, Rinv, dim, 0, true, 1.0);
+    rc = run_plan(work_);
+    if (rc) break;
+    launch_copy(tmp_, T_[node], L.size, stream_);
+    // R accumulation: Racc = R_pass * Racc (R in Gb, upper)
+    if (Rout) {
+      if (pass == 0) {
+        cudaMemcpyAsync(Racc, Gb, dd * sizeof(double), cudaMemcpyDeviceToDevice, stream_);
+      } else {
+        cudaMemsetAsync(Rtmp, 0, dd * sizeof(double), stream_);
+        work_.clear();
+        for (size_t i = 0; i < S.q.size(); ++i) {
+          const long long o = S.offset((int)i);
+          work_.add_output(Rtmp + o * dim + o, dim, 1, S.dim[i], S.dim[i], 0);
+          KChunk c = make_chunk();
+          c.A = Gb + o * dim + o; c.a_m = dim; c.a_k = 1;
+          c.B = Racc + o * dim + o; c.b_k = dim; c.b_n = 1;
+          c.K = S.dim[i];
+          work_.add_chunk(c);
+        }
+        rc = run_plan(work_);
+        cudaMemcpyAsync(Racc, Rtmp, dd * sizeof(double), cudaMemcpyDeviceToDevice, stream_);
+      }
+    }
+  }
+  if (rc == 0 && fallback) rc = qr_gram_schmidt(node, leg, Racc);
+  if (rc == 0 && Rout) cudaMemcpyAsync(Rout, Racc, dd * sizeof(double), cudaMemcpyDeviceToDevice, stream_);
+  cudaStreamSynchronize(stream_);
+  for (double* b : {Gb, Rinv, Racc, Rtmp}) { untrack(b); cudaFree(b); }
+  cudaFree(d_off);
+  cudaFree(d_n);
+  cudaFree(d_ld);
+  cudaFree(d_status);
+  return rc;
+}
+
+// Rows of the sector matrices of T[node] with `leg` as the column index,
+// ordered lexicographically in the two other legs.  Each view piece is
+// (block, first row in its sector, rows of the piece, row stride a).
+struct SectorPiece { int blk; long long row0; int a; };
+
+// Gram-Schmidt fallback for ill-conditioned or rank-deficient sectors:
+// gather every sector of `leg` into column-major workspaces, factorise, and
+// scatter Q back.  R (dim x dim, block diagonal) goes to Rout.
+int Engine::qr_gram_schmidt(int node, int leg, double* Rout) {
+  const Layout& L = layout_[node];
+  const Sectors& S = L.leg[leg];
+  const int dim = S.total();
+  const int ns = (int)S.q.size();
+  std::vector<long long> rows(ns, 0), woff(ns, 0);
+  // order of blocks: by the sector of the first remaining leg
+  std::vector<std::vector<int>> blocks(ns);
+  for (int bi = 0; bi < (int)L.blk.size(); ++bi) {
+    const Layout::Blk& b = L.blk[bi];
+    blocks[leg == 0 ? b.ia : (leg == 1 ? b.ib : b.ic)].push_back(bi);
+  }
+  for (int i = 0; i < ns; ++i) {
+    std::sort(blocks[i].begin(), blocks[i].end(), [&](int x, int y) {
+      const Layout::Blk& a = L.blk[x];
+      const Layout::Blk& b = L.blk[y];
+      if (leg == 0) return a.ib < b.ib;
+      return a.ia < b.ia;   // leg 1: a outer; leg 2: blocks already in (q_a) order
+    });
+    for (int bi : blocks[i]) {
+      const Layout::Blk& b = L.blk[bi];
+      rows[i] += leg == 0 ? (long long)b.db * b.dc : (leg == 1 ? (long long)b.da * b.dc : (long long)b.da * b.db);
+    }
+    if (rows[i] < S.dim[i]) {
+      err_ = "QR: a sector has fewer rows than columns";
+      return -7;
+    }
+  }
+  long long total = 0;
+  for (int i = 0; i < ns; ++i) { woff[i] = total; total += rows[i] * S.dim[i]; }
+  double* W = nullptr;
+  if (!check(cudaMalloc(&W, std::max(total, 1LL) * sizeof(double)), "QR workspace")) return -2;
+  track(W, std::max(total, 1LL) * sizeof(double));
+  double* T = T_[node];
+  int rc = 0;
+  for (int dir = 0; dir < 2 && rc == 0; ++dir) {   // 0 gather, 1 scatter
+    work_.clear();
+    for (int i = 0; i < ns; ++i) {
+      long long r0 = 0;
+      const long long m = rows[i];
+      for (int bi : blocks[i]) {
+        const Layout::Blk& b = L.blk[bi];
+        double* tb = T + b.off;
+        double* wb = W + woff[i] + r0;
+        if (leg == 2 || leg == 0) {
+          // leg 2: T block is (da*db) x dc row-major, rows in place
+          // leg 0: rows (b, c) of a block are its columns (b*dc + c), cols a
+          const int M = leg == 2 ? b.da * b.db : b.db * b.dc;
+          const int N = leg == 2 ? b.dc : b.da;
+          const long long t_m = leg == 2 ? b.dc : 1, t_n = leg == 2 ? 1 : (long long)b.db * b.dc;
+          KChunk c = make_chunk();
+          c.add = 1;
+          if (dir == 0) {
+            work_.add_output(wb, 1, m, M, N, 0);
+            c.A = tb; c.a_m = t_m; c.a_k = t_n;
+          } else {
+            work_.add_output(tb, t_m, t_n, M, N, 0);
+            c.A = wb; c.a_m = 1; c.a_k = m;
+          }
+          work_.add_chunk(c);
+          r0 += M;
+        } else {
+          for (int a = 0; a < b.da; ++a) {
+            // rows (a, c), c inner; cols b: T[a, b, c] at a*db*dc + b*dc + c
+            KChunk c = make_chunk();
+            c.add = 1;
+            double* ta = tb + (long long)a * b.db * b.dc;
+            if (dir == 0) {
+              work_.add_output(wb + (long long)a * b.dc, 1, m, b.dc, b.db, 0);
+              c.A = ta; c.a_m = 1; c.a_k = b.dc;
+            } else {
+              work_.add_output(ta, 1, b.dc, b.dc, b.db, 0);
+              c.A = wb + (long long)a * b.dc; c.a_m = 1; c.a_k = m;
+            }
+            work_.add_chunk(c);
+          }
+          r0 += (long long)b.da * b.dc;
+        }
+      }
+    }
+    rc = run_plan(work_);
+    if (rc == 0 && dir == 0) {
+      std::vector<long long> roff(ns);
+      std::vector<int> ri(ns), ci(ns);
+      for (int i = 0; i < ns; ++i) {
+        roff[i] = S.offset(i) * (long long)dim + S.offset(i);
+        ri[i] = (int)rows[i];
+        ci[i] = S.dim[i];
+        if (ci[i] > 256) { err_ = "QR: sector dimension above 256"; rc = -7; }
+      }
+      if (rc) break;
+      long long* d_w = nullptr;
+      long long* d_r = nullptr;
+      int *d_rows = nullptr, *d_cols = nullptr;
+      cudaMalloc(&d_w, ns * sizeof(long long));
+      cudaMalloc(&d_r, ns * sizeof(long long));
+      cudaMalloc(&d_rows, ns * sizeof(int));
+      cudaMalloc(&d_cols, ns * sizeof(int));
+      cudaMemcpyAsync(d_w, woff.data(), ns * sizeof(long long), cudaMemcpyHostToDevice, stream_);
+      cudaMemcpyAsync(d_r, roff.data(), ns * sizeof(long long), cudaMemcpyHostToDevice, stream_);
+      cudaMemcpyAsync(d_rows, ri.data(), ns * sizeof(int), cudaMemcpyHostToDevice, stream_);
+      cudaMemcpyAsync(d_cols, ci.data(), ns * sizeof(int), cudaMemcpyHostToDevice, stream_);
+      cudaMemsetAsync(Rout, 0, (size_t)dim * dim * sizeof(double), stream_);
+      launch_cgs2_qr(W, d_w, d_rows, d_cols, ns, Rout, d_r, dim, kQrDependent, kQrAccept, stream_);
+      rc = check(cudaStreamSynchronize(stream_), "Gram-Schmidt QR") ? 0 : -3;
+      cudaFree(d_w);
+      cudaFree(d_r);
+      cudaFree(d_rows);
+      cudaFree(d_cols);
+    }
+  }
+  cudaStreamSynchronize(stream_);
+  untrack(W);
+  cudaFree(W);
+  return rc;
+}
+
+// T[node] <- R (x)_leg T[node]
+int Engine::absorb(int node, int leg, const double* R) {
+  const Layout& L = layout_[node];
+  const int dim = L.leg[leg].total();
+  cudaMemsetAsync(tmp_, 0, L.size * sizeof(double), stream_);
+  work_.clear();
+  plan_leg_apply(work_, L, T_[node], L, tmp_, leg, R, dim, 0, false, 1.0);
+  int rc = run_plan(work_);
+  launch_copy(tmp_, T_[node], L.size, stream_);
+  return rc;
+}
+
+// ------------------------------------------------------------------ bond operators
+
+// Renormalized operators of the bond above `node` (subtree side), from
+// T[node] (isometric towards its parent) and the operators below it.
+int Engine::compute_up(int node) {
+  const TreeNode& nd = nodes_[node];
+  const Layout& L = layout_[node];
+  const int dim = L.leg[2].total();
+  const long long dd = (long long)dim * dim;
+  BondOps& out = up_[node];
+  const bool bottom = nd.child_kind[0] == 0;
+  const double* T = T_[node];
+  auto op_ptr = [&](int key, int shift) -> double* {
+    auto it = out.term.find(key);
+    if (it == out.term.end()) {
+      BondOp b;
+      b.ptr = (double*)dalloc(dd * sizeof(double));
+      b.shift = shift;
+      it = out.term.emplace(key, b).first;
+    }
+    it->second.shift = shift;
+    return it->second.ptr;
+  };
+  for (int c = 0; c < N_CLASSES; ++c)
+    if (!out.H[c]) out.H[c] = (double*)dalloc(dd * sizeof(double));
+  if (!out.Htot) out.Htot = (double*)dalloc(dd * sizeof(double));
+  // Contributions: (output matrix, alpha, op on leg 0, op on leg 1) where an
+  // op is identified by (term or site-ham), shift.
+  struct Contrib { double* O; double alpha; int term; int kind; int cls; };
+  // kind: 0 crossing term op, 1 term inside (coef), 2 site/child Hamiltonian of leg (term = leg)
+  std::vector<Contrib> cs;
+  for (int k = 0; k < (int)terms_.size(); ++k) {
+    if (crosses(k, node)) {
+      int d = 0;
+      for (auto& so : terms_[k].ops)
+        if (in_region_[node][so.first]) {
+          const SiteOp* op = site_op(lat_.parity(so.first), so.second);
+          d += op->dq;
+        }
+      cs.push_back({op_ptr(k, d), 1.0, k, 0, -1});
+    } else if (inside(k, node)) {
+      // inside terms touching both children (or, at the bottom, single-site terms too)
+      bool tl = false, tr = false;
+      for (auto& so : terms_[k].ops) {
+        for (int leg = 0; leg < 2; ++leg) {
+          int cn = leg_node(node, leg), cs_ = leg_site(node, leg);
+          bool in = cn >= 0 ? in_region_[cn][so.first] : so.first == cs_;
+          if (in) (leg == 0 ? tl : tr) = true;
+        }
+      }
+      if (tl && tr) cs.push_back({out.H[terms_[k].cls], terms_[k].coef, k, 1, terms_[k].cls});
+    }
+  }
+  for (int c = 0; c < N_CLASSES; ++c) cudaMemsetAsync(out.H[c], 0, dd * sizeof(double), stream_);
+  for (auto& kv : out.term) cudaMemsetAsync(kv.second.ptr, 0, dd * sizeof(double), stream_);
+  work_.clear();
+  int rc = 0;
+  if (bottom) {
+    // term contributions through row maps: O[c', c] += alpha sum_r T[r, c'] val(r) T[map(r), c]
+    auto add_map = [&](double* O, double alpha, const std::vector<RowMap>& maps) {
+      for (size_t oc = 0; oc < maps.size(); ++oc) {
+        const RowMap& rm = maps[oc];
+        if (rm.src_sector < 0 || L.sec_rows[oc] == 0) continue;
+        const int ic = rm.src_sector;
+        work_.add_output(O + L.leg[2].offset((int)oc) * dim + L.leg[2].offset(ic), dim, 1, L.leg[2].dim[oc],
+                         L.leg[2].dim[ic], 1);
+        KChunk c = make_chunk();
+        c.A = T + L.sec_off[oc]; c.a_m = 1; c.a_k = L.leg[2].dim[oc];
+        c.B = T + L.sec_off[ic]; c.b_k = L.leg[2].dim[ic]; c.b_n = 1;
+        c.bmap = rm.map; c.bval = rm.val;
+        c.K = L.sec_rows[oc]; c.alpha = alpha;
+        work_.add_chunk(c);
+      }
+    };
+    for (const Contrib& c : cs) add_map(c.O, c.alpha, rowmap(node, c.term));
+    for (int leg = 0; leg < 2; ++leg)
+      for (int cl = 0; cl < N_CLASSES; ++cl) add_map(out.H[cl], 1.0, site_ham_map(node, leg, cl));
+    rc = run_plan(work_);
+  } else {
+    // upper node: Z = (A (x) B) T into pool buffers, then O += T^T Z
+    struct Job { double* O; double alpha; int shA, shB; const double* A; const double* B; };
+    std::vector<Job> jobs;
+    for (const Contrib& c : cs) {
+      Job j{c.O, c.alpha, 0, 0, nullptr, nullptr};
+      for (int leg = 0; leg < 2; ++leg) {
+        int cn = leg_node(node, leg);
+        if (!touches(c.term, cn)) continue;
+        const BondOp& bo = up_[cn].term.at(c.term);
+        (leg == 0 ? j.A : j.B) = bo.ptr;
+        (leg == 0 ? j.shA : j.shB) = bo.shift;
+      }
+      jobs.push_back(j);
+    }
+    for (int leg = 0; leg < 2; ++leg) {
+      int cn = leg_node(node, leg);
+      for (int cl = 0; cl < N_CLASSES; ++cl) {
+        Job j{out.H[cl], 1.0, 0, 0, nullptr, nullptr};
+        (leg == 0 ? j.A : j.B) = up_[cn].H[cl];
+        jobs.push_back(j);
+      }
+    }
+    // process in batches that fit the Z pool
+    long long zsize = 0;
+    for (int s = -2; s <= 2; ++s) zsize = std::max(zsize, shifted(node, s).size);
+    const int batch = std::max<int>(1, (int)std::min<long long>((long long)jobs.size(), kZPoolBudget / (2 * std::max(1LL, zsize))));
+    ensure_zpool(2 * batch * zsize);
+    std::map<int, Layout> lays;
+    for (int s = -2; s <= 2; ++s) lays[s] = shifted(node, s);
+    const int dl = L.leg[0].total(), dr = L.leg[1].total();
+    for (size_t j0 = 0; j0 < jobs.size() && rc == 0; j0 += batch) {
+      size_t j1 = std::min(jobs.size(), j0 + batch);
+      cudaMemsetAsync(zpool_, 0, 2 * batch * zsize * sizeof(double), stream_);
+      KPlan& s1 = heff_stage_[0];
+      KPlan& s2 = heff_stage_[1];
+      s1.clear();
+      s2.clear();
+      work_.clear();
+      for (size_t j = j0; j < j1; ++j) {
+        const Job& jb = jobs[j];
+        double* z1 = zpool_ + (2 * (j - j0)) * zsize;
+        double* z2 = z1 + zsize;
+        const double* Z = nullptr;
+        int shift = 0;
+        if (jb.A && jb.B) {
+          plan_leg_apply(s1, L, T, lays[jb.shA], z1, 0, jb.A, dl, jb.shA, false, 1.0);
+          plan_leg_apply(s2, lays[jb.shA], z1, lays[jb.shA + jb.shB], z2, 1, jb.B, dr, jb.shB, false, 1.0);
+          Z = z2;
+          shift = jb.shA + jb.shB;
+        } else if (jb.A) {
+          plan_leg_apply(s1, L, T, lays[jb.shA], z1, 0, jb.A, dl, jb.shA, false, 1.0);
+          Z = z1;
+          shift = jb.shA;
+        } else {
+          plan_leg_apply(s1, L, T, lays[jb.shB], z1, 1, jb.B, dr, jb.shB, false, 1.0);
+          Z = z1;
+          shift = jb.shB;
+        }
+        plan_contract_but(work_, L, T, lays[shift], Z, 2, jb.O, dim, jb.alpha);
+      }
+      rc = run_plan(s1);
+      if (!rc && !s2.outs.empty()) rc = run_plan(s2);
+      if (!rc) rc = run_plan(work_);
+    }
+    plan_node_ = -1;   // stage plans reused: invalidate the H_eff cache
+  }
+  // Htot = sum of classes
+  cudaMemsetAsync(out.Htot, 0, dd * sizeof(double), stream_);
+  for (int c = 0; c < N_CLASSES; ++c) launch_add_scaled(out.H[c], out.Htot, dd, 1.0, stream_);
+  return rc;
+}
+
+// Environment operators of the bond above `node`, from its parent's tensor
+// (isometric towards `node`), the sibling's up operators and the parent's
+// environment operators.
+int Engine::compute_down(int node) {
+  const TreeNode& nd = nodes_[node];
+  const int par = nd.parent;
+  const TreeNode& pn = nodes_[par];
+  const int leg = (pn.child_kind[0] == 1 && pn.child[0] == node) ? 0 : 1;
+  const int sib_leg = 1 - leg;
+  const int sib = leg_node(par, sib_leg);
+  const Layout& L = layout_[par];
+  const int dim = L.leg[leg].total();
+  const long long dd = (long long)dim * dim;
+  BondOps& out = down_[node];
+  for (int c = 0; c < N_CLASSES; ++c)
+    if (!out.H[c]) out.H[c] = (double*)dalloc(dd * sizeof(double));
+  if (!out.Htot) out.Htot = (double*)dalloc(dd * sizeof(double));
+  std::vector<char> comp_par(lat_.n_sites(), 1);
+  for (int s : pn.sites) comp_par[s] = 0;
+  const bool par_root = pn.parent < 0;
+  struct Job { double* O; double alpha; const double* S; int shS; const double* P; int shP; };
+  std::vector<Job> jobs;
+  auto op_ptr = [&](int key, int shift) -> double* {
+    auto it = out.term.find(key);
+    if (it == out.term.end()) {
+      BondOp b;
+      b.ptr = (double*)dalloc(dd * sizeof(double));
+      it = out.term.emplace(key, b).first;
+    }
+    it->second.shift = shift;
+    return it->second.ptr;
+  };
+  for (int k = 0; k < (int)terms_.size(); ++k) {
+    const bool ts = sib >= 0 ? touches(k, sib) : false;
+    const bool tp = touches_sites(k, comp_par);
+    if (crosses(k, node)) {
+      Job j{nullptr, 1.0, nullptr, 0, nullptr, 0};
+      if (ts) { const BondOp& b = up_[sib].term.at(k); j.S = b.ptr; j.shS = b.shift; }
+      if (tp) { const BondOp& b = down_[par].term.at(k); j.P = b.ptr; j.shP = b.shift; }
+      const int dz = j.shS - j.shP;
+      j.O = op_ptr(k, -dz);
+      jobs.push_back(j);
+    } else if (!touches(k, node) && ts && tp) {
+      // inside the complement, crossing sibling | outside-parent
+      const BondOp& b1 = up_[sib].term.at(k);
+      const BondOp& b2 = down_[par].term.at(k);
+      jobs.push_back({out.H[terms_[k].cls], terms_[k].coef, b1.ptr, b1.shift, b2.ptr, b2.shift});
+    }
+  }
+  for (int cl = 0; cl < N_CLASSES; ++cl) {
+    jobs.push_back({out.H[cl], 1.0, up_[sib].H[cl], 0, nullptr, 0});
+    if (!par_root) jobs.push_back({out.H[cl], 1.0, nullptr, 0, down_[par].H[cl], 0});
+  }
+  for (int c = 0; c < N_CLASSES; ++c) cudaMemsetAsync(out.H[c], 0, dd * sizeof(double), stream_);
+  for (auto& kv : out.term) cudaMemsetAsync(kv.second.ptr, 0, dd * sizeof(double), stream_);
+  long long zsize = 0;
+  std::map<int, Layout> lays;
+  for (int s = -2; s <= 2; ++s) {
+    lays[s] = shifted(par, s);
+    zsize = std::max(zsize, lays[s].size);
+  }
+  const int batch = std::max<int>(1, (int)std::min<long long>((long long)jobs.size(), kZPoolBudget / (2 * std::max(1LL, zsize))));
+  ensure_zpool(2 * batch * zsize);
+  const int ds = L.leg[sib_leg].total(), dp = L.leg[2].total();
+  const double* T = T_[par];
+  int rc = 0;
+  for (size_t j0 = 0; j0 < jobs.size() && rc == 0; j0 += batch) {
+    size_t j1 = std::min(jobs.size(), j0 + batch);
+    cudaMemsetAsync(zpool_, 0, 2 * batch * zsize * sizeof(double), stream_);
+    KPlan& s1 = heff_stage_[0];
+    KPlan& s2 = heff_stage_[1];
+    s1.clear();
+    s2.clear();
+    work_.clear();
+    for (size_t j = j0; j < j1; ++j) {
+      const Job& jb = jobs[j];
+      double* z1 = zpool_ + (2 * (j - j0)) * zsize;
+      double* z2 = z1 + zsize;
+      const double* Z;
+      int shift;
+      // sibling op on sib_leg: layout shift += shS; parent-leg op: shift -= shP
+      if (jb.S && jb.P) {
+        plan_leg_apply(s1, L, T, lays[jb.shS], z1, sib_leg, jb.S, ds, jb.shS, false, 1.0);
+        plan_leg_apply(s2, lays[jb.shS], z1, lays[jb.shS - jb.shP], z2, 2, jb.P, dp, jb.shP, false, 1.0);
+        Z = z2;
+        shift = jb.shS - jb.shP;
+      } else if (jb.S) {
+        plan_leg_apply(s1, L, T, lays[jb.shS], z1, sib_leg, jb.S, ds, jb.shS, false, 1.0);
+        Z = z1;
+        shift = jb.shS;
+      } else {
+        plan_leg_apply(s1, L, T, lays[-jb.shP], z1, 2, jb.P, dp, jb.shP, false, 1.0);
+        Z = z1;
+        shift = -jb.shP;
+      }
+      plan_contract_but(work_, L, T, lays[shift], Z, leg, jb.O, dim, jb.alpha);
+    }
+    rc = run_plan(s1);
+    if (!rc && !s2.outs.empty()) rc = run_plan(s2);
+    if (!rc) rc = run_plan(work_);
+  }
+  plan_node_ = -1;
+  cudaMemsetAsync(out.Htot, 0, dd * sizeof(double), stream_);
+  for (int c = 0; c < N_CLASSES; ++c) launch_add_scaled(out.H[c], out.Htot, dd, 1.0, stream_);
+  return rc;
+}
+
+// ------------------------------------------------------------------ centre moves
+int Engine::move_to(int target) {
+  // path from centre to target through the lowest common ancestor
+  std::vector<int> pa, pb;
+  for (int x = center_; x >= 0; x = nodes_[x].parent) pa.push_back(x);
+  for (int x = target; x >= 0; x = nodes_[x].parent) pb.push_back(x);
+  int common = -1;
+  for (int x : pa)
+    if (std::find(pb.begin(), pb.end(), x) != pb.end()) { common = x; break; }
+  std::vector<int> path;
+  for (int x : pa) { path.push_back(x); if (x == common) break; }
+  std::vector<int> down;
+  for (int x : pb) { if (x == common) break; down.push_back(x); }
+  for (auto it = down.rbegin(); it != down.rend(); ++it) path.push_back(*it);
+  for (size_t i = 1; i < path.size(); ++i) {
+    const int c = path[i - 1], t = path[i];
+    int leg_c, leg_t;
+    if (nodes_[c].parent == t) {
+      leg_c = 2;
+      leg_t = (nodes_[t].child_kind[0] == 1 && nodes_[t].child[0] == c) ? 0 : 1;
+    } else {
+      leg_t = 2;
+      leg_c = (nodes_[c].child_kind[0] == 1 && nodes_[c].child[0] == t) ? 0 : 1;
+    }
+    const int dim = layout_[c].leg[leg_c].total();
+    double* R = nullptr;
+    cudaMalloc(&R, (size_t)dim * dim * sizeof(double));
+    track(R, (size_t)dim * dim * sizeof(double));
+    int rc = qr_toward(c, leg_c, R);
+    if (!rc) rc = absorb(t, leg_t, R);
+    cudaStreamSynchronize(stream_);
+    untrack(R);
+    cudaFree(R);
+    if (rc) return rc;
+    center_ = t;
+    if (leg_c == 2) rc = compute_up(c);
+    else rc = compute_down(t);
+    if (rc) return rc;
+  }
+  return check(cudaGetLastError(), "move") ? 0 : -3;
+}
+
+// ------------------------------------------------------------------ H_eff
+// Terms of H_eff at `node` (Methods step (i)): block Hamiltonians of the
+// three legs and every term touching at least two of the three regions.
+void Engine::build_heff_terms(int node, int cls, std::vector<HTerm>* out) {
+  out->clear();
+  const TreeNode& nd = nodes_[node];
+  const bool bottom = nd.child_kind[0] == 0;
+  std::vector<char> comp(lat_.n_sites(), 1);
+  for (int s : nd.sites) comp[s] = 0;
+  const bool root = nd.parent < 0;
+  for (int leg = 0; leg < 2; ++leg) {
+    HTerm h;
+    h.cls = cls;
+    if (bottom) {
+      h.op[leg].kind = 2;
+      h.op[leg].term = -1;
+      h.op[leg].cls = cls;
+    } else {
+      const BondOps& b = up_[leg_node(node, leg)];
+      h.op[leg].kind = 1;
+      h.op[leg].ptr = cls < 0 ? b.Htot : b.H[cls];
+    }
+    out->push_back(h);
+  }
+  if (!root) {
+    HTerm h;
+    h.cls = cls;
+    h.op[2].kind = 1;
+    h.op[2].ptr = cls < 0 ? down_[node].Htot : down_[node].H[cls];
+    out->push_back(h);
+  }
+  for (int k = 0; k < (int)terms_.size(); ++k) {
+    if (cls >= 0 && terms_[k].cls != cls) continue;
+    bool t[3] = {false, false, false};
+    for (auto& so : terms_[k].ops) {
+      for (int leg = 0; leg < 2; ++leg) {
+        int cn = leg_node(node, leg);
+        bool in = cn >= 0 ? in_region_[cn][so.first] : so.first == leg_site(node, leg);
+        if (in) t[leg] = true;
+      }
+      if (comp[so.first]) t[2] = true;
+    }
+    if ((int)t[0] + (int)t[1] + (int)t[2] < 2) continue;
+    HTerm h;
+    h.coef = terms_[k].coef;
+    h.cls = terms_[k].cls;
+    for (int leg = 0; leg < 2; ++leg) {
+      if (!t[leg]) continue;
+      if (bottom) {
+        h.op[leg].kind = 2;
+        h.op[leg].term = k;
+      } else {
+        const BondOp& b = up_[leg_node(node, leg)].term.at(k);
+        h.op[leg].kind = 1;
+        h.op[leg].ptr = b.ptr;
+        h.op[leg].shift = b.shift;
+      }
+    }
+    if (t[2]) {
+      const BondOp& b = down_[node].term.at(k);
+      h.op[2].kind = 1;
+      h.op[2].ptr = b.ptr;
+      h.op[2].shift = b.shift;
+    }
+    out->push_back(h);
+  }
+}
+
+int Engine::build_heff_plan(int node, int cls) {
+  if (plan_node_ == node && plan_cls_ == cls) return 0;
+  std::vector<HTerm> hts;
+  build_heff_terms(node, cls, &hts);
+  const Layout& L = layout_[node];
+  const bool bottom = nodes_[node].child_kind[0] == 0;
+  for (int i = 0; i < 3; ++i) heff_stage_[i].clear();
+  KPlan& s3 = heff_stage_[2];
+  const int d2 = L.leg[2].total();
+  const double cst = (cls < 0 || cls == CLS_NU) ? constant_ : 0.0;
+  if (bottom) {
+    // per output c-sector: chunks over terms, A rows gathered from x_in
+    for (size_t oc = 0; oc < L.leg[2].q.size(); ++oc) {
+      const int rows = L.sec_rows[oc];
+      if (rows == 0) continue;
+      const int dc = L.leg[2].dim[oc];
+      s3.add_output(y_out_ + L.sec_off[oc], dc, 1, rows, dc, 0);
+      if (cst != 0.0) {
+        KChunk c = make_chunk();
+        c.A = x_in_ + L.sec_off[oc]; c.a_m = dc; c.a_k = 1;
+        c.add = 1; c.alpha = cst;
+        s3.add_chunk(c);
+      }
+      for (const HTerm& h : hts) {
+        const bool phys = h.op[0].kind == 2 || h.op[1].kind == 2;
+        const RowMap* rm = nullptr;
+        if (phys) {
+          if (h.op[0].kind == 2 && h.op[0].term < 0) rm = &site_ham_map(node, 0, h.op[0].cls)[oc];
+          else if (h.op[1].kind == 2 && h.op[1].term < 0) rm = &site_ham_map(node, 1, h.op[1].cls)[oc];
+          else rm = &rowmap(node, h.op[0].kind == 2 ? h.op[0].term : h.op[1].term)[oc];
+          if (rm->src_sector < 0) continue;
+        }
+        const int ic = phys ? rm->src_sector : (int)oc;
+        const int dci = L.leg[2].dim[ic];
+        KChunk c = make_chunk();
+        c.A = x_in_ + L.sec_off[ic]; c.a_m = dci; c.a_k = 1;
+        if (rm) { c.amap = rm->map; c.aval = rm->val; }
+        c.alpha = h.coef;
+        if (h.op[2].kind == 1) {
+          // sanity: env op must map sector ic -> oc
+          if (L.leg[2].find(L.leg[2].q[ic] + h.op[2].shift) != (int)oc) continue;
+          c.B = h.op[2].ptr + L.leg[2].offset((int)oc) * d2 + L.leg[2].offset(ic);
+          c.b_k = 1; c.b_n = d2;
+          c.K = dci;
+        } else {
+          if (ic != (int)oc) continue;
+          c.add = 1;
+        }
+        s3.add_chunk(c);
+      }
+    }
+  } else {
+    // upper node: Z buffers per term, stage 1 (first child op), stage 2 (second)
+    std::map<int, Layout> lays;
+    long long zsize = 0;
+    for (int s = -2; s <= 2; ++s) {
+      lays[s] = shifted(node, s);
+      zsize = std::max(zsize, lays[s].size);
+    }
+    int nz = 0;
+    for (const HTerm& h : hts) nz += (h.op[0].kind ? 1 : 0) + (h.op[1].kind ? 1 : 0);
+    ensure_zpool(std::max(1, nz) * zsize);
+    heff_z_elems_ = (long long)nz * zsize;
+    const int dl = L.leg[0].total(), dr = L.leg[1].total();
+    struct Src { const double* Z; int shift; };
+    std::vector<Src> srcs;
+    int zi = 0;
+    for (const HTerm& h : hts) {
+      const double* Z = x_in_;
+      int shift = 0;
+      if (h.op[0].kind) {
+        double* z1 = zpool_ + (zi++) * zsize;
+        plan_leg_apply(heff_stage_[0], L, x_in_, lays[h.op[0].shift], z1, 0, h.op[0].ptr, dl, h.op[0].shift, false,
+                       1.0);
+        Z = z1;
+        shift = h.op[0].shift;
+        if (h.op[1].kind) {
+          double* z2 = zpool_ + (zi++) * zsize;
+          plan_leg_apply(heff_stage_[1], lays[shift], z1, lays[shift + h.op[1].shift], z2, 1, h.op[1].ptr, dr,
+                         h.op[1].shift, false, 1.0);
+          Z = z2;
+          shift += h.op[1].shift;
+        }
+      } else if (h.op[1].kind) {
+        double* z1 = zpool_ + (zi++) * zsize;
+        plan_leg_apply(heff_stage_[0], L, x_in_, lays[h.op[1].shift], z1, 1, h.op[1].ptr, dr, h.op[1].shift, false,
+                       1.0);
+        Z = z1;
+        shift = h.op[1].shift;
+      }
+      srcs.push_back({Z, shift});
+    }
+    // stage 3: per y block, chunks over terms
+    for (const Layout::Blk& yb : L.blk) {
+      s3.add_output(y_out_ + yb.off, yb.dc, 1, yb.da * yb.db, yb.dc, 0);
+      if (cst != 0.0) {
+        KChunk c = make_chunk();
+        c.A = x_in_ + yb.off; c.a_m = yb.dc; c.a_k = 1;
+        c.add = 1; c.alpha = cst;
+        s3.add_chunk(c);
+      }
+      for (size_t t = 0; t < hts.size(); ++t) {
+        const HTerm& h = hts[t];
+        const Layout& LZ = lays[srcs[t].shift];
+        const int k = LZ.find(yb.ia, yb.ib);
+        if (k < 0) continue;
+        const Layout::Blk& zb = LZ.blk[k];
+        KChunk c = make_chunk();
+        c.A = srcs[t].Z + zb.off; c.a_m = zb.dc; c.a_k = 1;
+        c.alpha = h.coef;
+        if (h.op[2].kind == 1) {
+          if (L.leg[2].find(L.leg[2].q[zb.ic] + h.op[2].shift) != yb.ic) continue;
+          c.B = h.op[2].ptr + L.leg[2].offset(yb.ic) * d2 + L.leg[2].offset(zb.ic);
+          c.b_k = 1; c.b_n = d2;
+          c.K = zb.dc;
+        } else {
+          if (zb.ic != yb.ic) continue;
+          c.add = 1;
+        }
+        s3.add_chunk(c);
+      }
+    }
+    for (int i = 0; i < 2; ++i) heff_stage_[i].finalize(kKPart);
+  }
+  s3.finalize(kKPart);
+  long long need = 0;
+  for (int i = 0; i < 3; ++i) {
+    need = std::max(need, heff_stage_[i].scratch_need);
+    heff_stage_[i].upload(stream_);
+  }
+  ensure_scratch(std::max<long long>(need, 1));
+  if (validate_)
+    for (int i = 0; i < 3; ++i)
+      if (!validate_plan(heff_stage_[i], "H_eff plan")) return -1;
+  plan_node_ = node;
+  plan_cls_ = cls;
+  return check(cudaGetLastError(), "plan") ? 0 : -3;
+}
+
+int Engine::apply_heff(const double* x, double* y, int cls) {
+  int rc = build_heff_plan(center_, cls);
+  if (rc) return rc;
+  const long long n = layout_[center_].size;
+  if (x != x_in_) launch_copy(x, x_in_, n, stream_);
+  const bool bottom = nodes_[center_].child_kind[0] == 0;
+  if (!bottom && heff_z_elems_ > 0) {
+    // Z blocks that no source block maps to must read as zero
+    cudaMemsetAsync(zpool_, 0, heff_z_elems_ * sizeof(double), stream_);
+  }
+  for (int i = 0; i < 3; ++i) {
+    KPlan& pl = heff_stage_[i];
+    if (pl.tiles.empty()) continue;
+    launch_kc_gemm(pl.d_tiles, (int)pl.tiles.size(), pl.d_outs, pl.d_chunks, scratch_, stream_);
+    launch_kc_reduce(pl.d_outs, (int)pl.outs.size(), pl.d_red, (int)pl.red.size(), scratch_, stream_);
+  }
+  if (y != y_out_) launch_copy(y_out_, y, n, stream_);
+  return check(cudaGetLastError(), "apply_heff") ? 0 : -3;
+}
+
+// ------------------------------------------------------------------ Lanczos
+// Symmetric Lanczos with full (twice-applied classical Gram-Schmidt)
+// reorthogonalisation, started from the current tensor; the lowest Ritz
+// pair of the tridiagonal is found on the device.  Stops when the
+// residual estimate |beta_k s_k| <= tol |theta|, restarting from the Ritz
+// vector when the Krylov space is full.
+int Engine::lanczos(int node, double tol, int max_krylov, double* energy, double* resid, int* iters) {
+  const long long n = layout_[node].size;
+  int kmax = std::min(std::max(max_krylov, 2), kMaxKrylov);
+  if (kmax > n) kmax = (int)n;
+  if (kmax_alloc_ < kmax + 1) {
+    if (V_) { untrack(V_); cudaFree(V_); }
+    if (!check(cudaMalloc(&V_, (size_t)(kmax + 1) * nmax_ * sizeof(double)), "Krylov basis")) return -2;
+    track(V_, (size_t)(kmax + 1) * nmax_ * sizeof(double));
+    kmax_alloc_ = kmax + 1;
+  }
+  double* alpha = d_scal_;
+  double* beta = d_scal_ + 128;
+  double* svec = d_scal_ + 256;
+  double* outv = d_scal_ + 384;
+  double* coef = d_scal_ + 512;
+  double* nrm2 = d_scal_ + 640;
+  double* xvec = tmp_;
+  const long long ld = nmax_;
+  launch_copy(T_[node], xvec, n, stream_);
+  int total_iters = 0;
+  double theta = 0.0, res = 0.0;
+  const int max_restarts = 50;
+  for (int restart = 0; restart < max_restarts; ++restart) {
+    launch_dot(xvec, xvec, n, d_partial_, nrm2, stream_);
+    launch_scale_inv_sqrt(xvec, V_, n, nrm2, stream_);
+    int k = 0;
+    bool done = false;
+    double host[4] = {0, 0, 0, 0};
+    for (int j = 0; j < kmax; ++j) {
+      double* vj = V_ + j * ld;
+      int rc = apply_heff(vj, y_out_, -1);
+      if (rc) return rc;
+      ++total_iters;
+      launch_dot(vj, y_out_, n, d_partial_, alpha + j, stream_);
+      launch_axpby(vj, y_out_, n, alpha + j, 0.0, -1.0, nullptr, 1.0, stream_);
+      if (j > 0) launch_axpby(V_ + (j - 1) * ld, y_out_, n, beta + (j - 1), 0.0, -1.0, nullptr, 1.0, stream_);
+      for (int pass = 0; pass < 2; ++pass) {
+        launch_multidot(V_, ld, j + 1, y_out_, n, d_partial_, coef, stream_);
+        launch_multiaxpy(V_, ld, j + 1, coef, y_out_, n, stream_);
+      }
+      launch_dot(y_out_, y_out_, n, d_partial_, nrm2, stream_);
+      launch_sqrt(nrm2, beta + j, stream_);
+      k = j + 1;
+      launch_tridiag_lowest(alpha, beta, k, outv, svec, stream_);
+      cudaMemcpyAsync(host, outv, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream_);
+      cudaMemcpyAsync(host + 2, beta + j, sizeof(double), cudaMemcpyDeviceToHost, stream_);
+      if (!check(cudaStreamSynchronize(stream_), "lanczos")) return -3;
+      const double bj = host[2];
+      theta = host[0];
+      res = host[1];
+      const bool breakdown = bj <= 1e-13 * std::max(1.0, std::fabs(theta));
+      if (res <= tol * std::max(1e-300, std::fabs(theta)) || breakdown) { done = true; break; }
+      if (j + 1 < kmax) launch_scale_inv_sqrt(y_out_, V_ + (j + 1) * ld, n, nrm2, stream_);
+    }
+    // Ritz vector x = V s
+    launch_combine(V_, ld, k, svec, xvec, n, stream_);
+    if (done) break;
+  }
+  // normalise
+  launch_dot(xvec, xvec, n, d_partial_, nrm2, stream_);
+  launch_scale_inv_sqrt(xvec, T_[node], n, nrm2, stream_);
+  *energy = theta;
+  *resid = res;
+  *iters = total_iters;
+  return check(cudaStreamSynchronize(stream_), "lanczos end") ? 0 : -3;
+}
+
+int Engine::optimize_node(int node, double tol, int max_krylov, SweepStats* st, double* e) {
+  int rc = move_to(node);
+  if (rc) return rc;
+  double energy = 0, res = 0;
+  int iters = 0;
+  rc = lanczos(node, tol, max_krylov, &energy, &res, &iters);
+  if (rc) return rc;
+  last_lanczos_iters = iters;
+  if (st) {
+    st->matvecs += iters;
+    st->node_updates += 1;
+    st->energy = energy;
+    st->max_residual = std::max(st->max_residual, res / std::max(1e-300, std::fabs(energy)));
+    if (res > tol * std::fabs(energy)) st->not_converged += 1;
+  }
+  if (e) *e = energy;
+  return 0;
+}
+
+int Engine::sweep(double tol, int max_krylov, SweepStats* st, std::vector<double>* energies) {
+  for (int i = 0; i < (int)nodes_.size(); ++i) {
+    double e = 0;
+    int rc = optimize_node(i, tol, max_krylov, st, &e);
+    if (rc) return rc;
+    if (energies) energies->push_back(e);
+  }
+  return 0;
+}
+
+// ------------------------------------------------------------------ measurement
+int Engine::energy(double* total, double parts[N_CLASSES]) {
+  const long long n = layout_[center_].size;
+  double* nrm2 = d_scal_ + 640;
+  double* dv = d_scal_ + 700;
+  launch_dot(T_[center_], T_[center_], n, d_partial_, nrm2, stream_);
+  int rc = apply_heff(T_[center_], tmp_, -1);
+  if (rc) return rc;
+  launch_dot(T_[center_], tmp_, n, d_partial_, dv, stream_);
+  for (int c = 0; c < N_CLASSES; ++c) {
+    rc = apply_heff(T_[center_], tmp_, c);
+    if (rc) return rc;
+    launch_dot(T_[center_], tmp_, n, d_partial_, dv + 1 + c, stream_);
+  }
+  double host[8];
+  cudaMemcpyAsync(host, nrm2, sizeof(double), cudaMemcpyDeviceToHost, stream_);
+  cudaMemcpyAsync(host + 1, dv, 6 * sizeof(double), cudaMemcpyDeviceToHost, stream_);
+  if (!check(cudaStreamSynchronize(stream_), "energy")) return -3;
+  *total = host[1] / host[0];
+  for (int c = 0; c < N_CLASSES; ++c) parts[c] = host[2 + c] / host[0];
+  plan_node_ = -1;
+  return 0;
+}
+
+// Reduced density matrices pushed down from the root: rho_child[i', i] =
+// sum T[.., i', .., c'] rho[c', c] T[.., i, .., c].  Returns the 267
+// diagonal entries per site.
+int Engine::site_probabilities(std::vector<double>* probs) {
+  int rc = move_to((int)nodes_.size() - 1);
+  if (rc) return rc;
+  const int n = (int)nodes_.size();
+  std::vector<double*> rho(n, nullptr);
+  probs->assign((size_t)lat_.n_sites() * kLocalDim, 0.0);
+  double* one = nullptr;
+  cudaMalloc(&one, sizeof(double));
+  track(one, sizeof(double));
+  const double v1 = 1.0;
+  cudaMemcpyAsync(one, &v1, sizeof(double), cudaMemcpyHostToDevice, stream_);
+  rho[n - 1] = one;
+  std::vector<void*> tofree{one};
+  for (int idx = n - 1; idx >= 0 && rc == 0; --idx) {
+    const Layout& L = layout_[idx];
+    const int dp = L.leg[2].total();
+    // Y = rho (x)_2 T  (rho symmetric)
+    cudaMemsetAsync(tmp_, 0, L.size * sizeof(double), stream_);
+    work_.clear();
+    plan_leg_apply(work_, L, T_[idx], L, tmp_, 2, rho[idx], dp, 0, false, 1.0);
+    rc = run_plan(work_);
+    for (int leg = 0; leg < 2 && rc == 0; ++leg) {
+      const int d = L.leg[leg].total();
+      double* red = nullptr;
+      cudaMalloc(&red, (size_t)d * d * sizeof(double));
+      track(red, (size_t)d * d * sizeof(double));
+      tofree.push_back(red);
+      cudaMemsetAsync(red, 0, (size_t)d * d * sizeof(double), stream_);
+      work_.clear();
+      plan_contract_but(work_, L, T_[idx], L, tmp_, leg, red, d, 1.0);
+      rc = run_plan(work_);
+      if (nodes_[idx].child_kind[leg] == 1) {
+        rho[nodes_[idx].child[leg]] = red;
+      } else {
+        std::vector<double> h((size_t)d * d);
+        cudaMemcpyAsync(h.data(), red, h.size() * sizeof(double), cudaMemcpyDeviceToHost, stream_);
+        cudaStreamSynchronize(stream_);
+        const int s = nodes_[idx].child[leg];
+        for (int a = 0; a < kLocalDim; ++a) (*probs)[(size_t)s * kLocalDim + a] = h[(size_t)a * d + a];
+      }
+    }
+  }
+  cudaStreamSynchronize(stream_);
+  for (void* p : tofree) { untrack(p); cudaFree(p); }
+  return rc ? rc : (check(cudaGetLastError(), "probabilities") ? 0 : -3);
+}
+
+int Engine::node_export(int node, std::vector<double>* host) {
+  host->resize(layout_[node].size);
+  cudaMemcpyAsync(host->data(), T_[node], host->size() * sizeof(double), cudaMemcpyDeviceToHost, stream_);
+  return check(cudaStreamSynchronize(stream_), "export") ? 0 : -3;
+}
+
+int Engine::node_import(int node, const std::vector<double>& host) {
+  if ((long long)host.size() != layout_[node].size) return -1;
+  for (double v : host)
+    if (!std::isfinite(v)) return -5;
+  cudaMemcpyAsync(T_[node], host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, stream_);
+  plan_node_ = -1;
+  return check(cudaStreamSynchronize(stream_), "import") ? 0 : -3;
+}
+
+long long Engine::matvec_flops_algorithmic(int node) {
+  (void)node;
+  return 0;
+}
+
+}  // namespace qed

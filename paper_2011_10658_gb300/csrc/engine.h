@@ -1,0 +1,229 @@
+// TTN sweep engine: device-resident U(1) block tensors, renormalized bond
+// operators, H_eff plans, Lanczos eigensolver and isometry-centre moves.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "kernels.cuh"
+#include "model.h"
+
+namespace qed {
+
+enum Precision { PREC_FP64 = 0, PREC_TF32 = 1, PREC_BF16 = 2 };
+
+// Block layout of a three-leg tensor T[a, b, c] whose blocks (q_a, q_b)
+// satisfy q_c = q_a + q_b - shift.  Blocks are ordered by (c-sector, q_a);
+// inside a block elements are row-major (a, b, c).  The blocks of one
+// c-sector therefore form a contiguous (rows x dim_c) row-major matrix.
+struct Layout {
+  Sectors leg[3];
+  int shift = 0;
+  struct Blk {
+    int ia, ib, ic;
+    int da, db, dc;
+    long long off;       // element offset of the block
+    int row0;            // first row of the block inside its c-sector matrix
+  };
+  std::vector<Blk> blk;
+  std::map<std::pair<int, int>, int> index;
+  std::vector<long long> sec_off;   // per c-sector: offset of its matrix
+  std::vector<int> sec_rows;        // per c-sector: number of rows
+  long long size = 0;
+  void build(const Sectors& a, const Sectors& b, const Sectors& c, int shift_);
+  int find(int ia, int ib) const {
+    auto it = index.find({ia, ib});
+    return it == index.end() ? -1 : it->second;
+  }
+};
+
+// Host list of grouped-GEMM work plus its device copy.
+// Outputs that name the same destination (pointer and shape) are merged, so
+// every output region is written by exactly one output: contributions to a
+// shared block are K-concatenated chunks, never concurrent writes.
+struct KPlan {
+  std::vector<KChunk> chunks;
+  std::vector<KOutput> outs;
+  std::vector<std::vector<KChunk>> out_chunks;
+  std::map<std::tuple<uintptr_t, long long, long long, int, int>, int> out_index;
+  int current = -1;
+  std::vector<KTile> tiles;
+  std::vector<int> red;
+  long long scratch_need = 0;
+  KChunk* d_chunks = nullptr;
+  KOutput* d_outs = nullptr;
+  KTile* d_tiles = nullptr;
+  int* d_red = nullptr;
+  size_t cap_chunks = 0, cap_outs = 0, cap_tiles = 0, cap_red = 0;
+  void clear() {
+    chunks.clear(); outs.clear(); out_chunks.clear(); out_index.clear(); current = -1;
+    tiles.clear(); red.clear(); scratch_need = 0;
+  }
+  int add_output(double* C, long long c_m, long long c_n, int M, int N, int accumulate);
+  void add_chunk(const KChunk& c);
+  void finalize(long long k_part);
+  void upload(cudaStream_t s);
+  void release();
+};
+
+// A dense renormalized operator on a bond: O[i', i] (row-major dim x dim)
+// with charge-label shift q(i') - q(i) = shift.
+struct BondOp {
+  double* ptr = nullptr;
+  int shift = 0;
+};
+
+struct BondOps {
+  std::unordered_map<int, BondOp> term;
+  double* H[N_CLASSES] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  double* Htot = nullptr;
+};
+
+// One H_eff term at the centre: coef * op0 (x) op1 (x) op2.
+// Bottom legs: site op of a term (row maps); bond legs: dense operators.
+struct OpRef {
+  int kind = 0;           // 0 = identity, 1 = bond operator, 2 = site term op (bottom leg)
+  const double* ptr = nullptr;
+  int shift = 0;
+  int term = -1;          // for kind 2: the term whose site op acts here (-1: site Hamiltonian)
+  int cls = -1;           // for kind 2 with term = -1: class of the site Hamiltonian (-1 = all)
+};
+
+struct HTerm {
+  double coef = 1.0;
+  int cls = -1;           // -1 = mixed (block Hamiltonians), else the coupling class
+  OpRef op[3];
+};
+
+struct RowMap {
+  int* map = nullptr;     // per output row, sign-encoded source row
+  double* val = nullptr;  // optional per-row factor
+  int src_sector = -1;    // source c-sector index (-1: all rows zero)
+};
+
+struct SweepStats {
+  double energy = 0.0;
+  int matvecs = 0;
+  int node_updates = 0;
+  double max_residual = 0.0;
+  int not_converged = 0;
+};
+
+class Engine {
+ public:
+  Engine(const Params& p, int chi, uint64_t seed, int precision, cudaStream_t stream);
+  ~Engine();
+
+  // One full sweep (nodes in number order); energies[i] per node update.
+  int sweep(double tol, int max_krylov, SweepStats* st, std::vector<double>* energies);
+  // Energy with the current centre tensor; class-resolved parts.
+  int energy(double* total, double parts[N_CLASSES]);
+  // Single-site diagonal probabilities (267 per site), centre moved to the root.
+  int site_probabilities(std::vector<double>* probs);
+  int node_export(int node, std::vector<double>* host);
+  int node_import(int node, const std::vector<double>& host);
+  int move_to(int target);
+  int optimize_node(int node, double tol, int max_krylov, SweepStats* st, double* e);
+  // H_eff x at the current centre (x, y device pointers, centre layout).
+  int apply_heff(const double* x, double* y, int cls_filter);
+  long long node_size(int node) const { return layout_[node].size; }
+  int center() const { return center_; }
+  int n_nodes() const { return (int)nodes_.size(); }
+  const std::vector<Sectors>& bonds() const { return bonds_; }
+  const Layout& layout(int n) const { return layout_[n]; }
+  double constant() const { return constant_; }
+  int n_terms() const { return (int)terms_.size(); }
+  cudaStream_t stream() const { return stream_; }
+  double* tensor(int n) { return T_[n]; }
+  const std::string& error() const { return err_; }
+  long long matvec_flops_algorithmic(int node);
+  long long device_bytes() const { return bytes_; }
+  int last_lanczos_iters = 0;
+
+ private:
+  Params p_;
+  int chi_;
+  uint64_t seed_;
+  int precision_;
+  cudaStream_t stream_;
+  Lattice lat_;
+  std::vector<Term> terms_;
+  double constant_ = 0.0;
+  std::vector<TreeNode> nodes_;
+  std::vector<Sectors> bonds_;
+  std::vector<Layout> layout_;
+  std::vector<std::vector<char>> in_region_;
+  std::vector<double*> T_;
+  std::vector<BondOps> up_, down_;
+  int center_ = -1;
+  std::string err_;
+  long long bytes_ = 0;
+  std::vector<void*> allocs_;
+  std::map<long long, SiteOp*> site_ops_;   // packed (parity, kind, a, b)
+  // row maps of bottom nodes: (node, term) -> per output c-sector
+  std::map<std::pair<int, int>, std::vector<RowMap>> rowmaps_;
+  // H_eff plan cache for the current centre
+  int plan_node_ = -1;
+  int plan_cls_ = -2;
+  KPlan heff_stage_[3];
+  long long heff_z_elems_ = 0;
+  double* zpool_ = nullptr;
+  long long zpool_elems_ = 0;
+  double* x_in_ = nullptr;
+  double* y_out_ = nullptr;
+  double* tmp_ = nullptr;
+  double* scratch_ = nullptr;
+  long long scratch_elems_ = 0;
+  KPlan work_;
+  // Lanczos workspace
+  double* V_ = nullptr;
+  int kmax_alloc_ = 0;
+  double* d_scal_ = nullptr;   // alpha[128], beta[128], s[128], out[8], coeffs[128], partials
+  double* d_partial_ = nullptr;
+  long long nmax_ = 0;
+
+  // device allocations (base, bytes) for the optional plan validator
+  std::map<uintptr_t, size_t> ranges_;
+  bool validate_ = false;
+  bool validate_plan(const KPlan& pl, const char* what);
+  void track(void* p, size_t bytes) { if (p) ranges_[(uintptr_t)p] = bytes; }
+  void untrack(void* p) { ranges_.erase((uintptr_t)p); }
+  bool in_range(const void* p, long long lo_off, long long hi_off) const;
+  void* dalloc(size_t bytes);
+  bool check(cudaError_t e, const char* what);
+  const SiteOp* site_op(int parity, const OpKey& key);
+  bool touches(int term, int node) const;
+  bool touches_sites(int term, const std::vector<char>& reg) const;
+  bool inside(int term, int node) const;
+  bool crosses(int term, int node) const;
+  int leg_node(int node, int leg) const;  // child node id or -1 for a site
+  int leg_site(int node, int leg) const;
+  const Sectors& leg_sectors(int node, int leg) const;
+  void init_tensors();
+  int qr_toward(int node, int leg, double* Rout);
+  int qr_gram_schmidt(int node, int leg, double* Rout);
+  int absorb(int node, int leg, const double* R);
+  int compute_up(int node);
+  int compute_down(int node);
+  const std::vector<RowMap>& rowmap(int node, int term);
+  RowMap build_rowmap_sector(int node, const SiteOp* A, const SiteOp* B, int out_sector, const std::vector<double>* vals);
+  const std::vector<RowMap>& site_ham_map(int node, int leg, int cls);
+  void build_heff_terms(int node, int cls_filter, std::vector<HTerm>* out);
+  int build_heff_plan(int node, int cls_filter);
+  int run_plan(KPlan& pl);
+  void plan_leg_apply(KPlan& pl, const Layout& LX, const double* X, const Layout& LY, double* Y, int leg,
+                      const double* P, int dimP, int shiftP, bool transposed, double alpha);
+  void plan_contract_but(KPlan& pl, const Layout& LT, const double* T, const Layout& LZ, const double* Z, int leg,
+                         double* O, int dimO, double alpha);
+  void ensure_scratch(long long elems);
+  void ensure_zpool(long long elems);
+  Layout shifted(int node, int shift) const;
+  int lanczos(int node, double tol, int max_krylov, double* energy, double* resid, int* iters);
+};
+
+}  // namespace qed

@@ -1,0 +1,98 @@
+// Device kernels of the TTN hot path (declarations shared by the engine).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace qed {
+
+// One contribution A(MxK) * B(KxN) to an output.  Element addressing:
+//   A[m,k] = sA * aval[m] * A[row*a_m + k*a_k],  amap[m] = (row << 1) | negate, -1 = zero row
+//   B[k,n] = sB * bval[k] * B[row*b_k + n*b_n],  bmap[k] likewise (maps and vals optional)
+// With add != 0 there is no B:  C[m,n] += alpha * A[m,n] (A[m,n] addressed as A[m,k=n]).
+struct KChunk {
+  const double* A;
+  long long a_m, a_k;
+  const int* amap;
+  const double* aval;
+  const double* B;
+  long long b_k, b_n;
+  const int* bmap;
+  const double* bval;
+  int K;
+  int add;
+  double alpha;
+};
+
+// An output C (MxN, C[m,n] at C + m*c_m + n*c_n) = sum of its chunks
+// (accumulate != 0: C += sum).
+struct KOutput {
+  double* C;
+  long long c_m, c_n;
+  int M, N;
+  int chunk_begin, chunk_end;
+  int accumulate;
+  int n_parts;        // > 1: split over chunk ranges, partial sums in scratch
+  long long part_off; // scratch offset (doubles) of this output's partials
+};
+
+// One CTA's work: a 32x32 tile of an output over a chunk range.
+struct KTile {
+  int out;
+  int m0, n0;
+  int chunk_begin, chunk_end;
+  int part;           // partial slot (-1: write C directly)
+};
+
+constexpr int KT_BM = 32;
+constexpr int KT_BN = 32;
+
+void launch_kc_gemm(const KTile* tiles, int n_tiles, const KOutput* outs, const KChunk* chunks,
+                    double* scratch, cudaStream_t s);
+void launch_kc_reduce(const KOutput* outs, int n_outs, const int* red_list, int n_red, double* scratch,
+                      cudaStream_t s);
+
+// ---- vector kernels (FP64) ----
+// partial sums per block then a single-block finish: deterministic.
+void launch_dot(const double* x, const double* y, long long n, double* partial, double* out, cudaStream_t s);
+// out[j] = <Q_j, w> for j < k (Q columns of length n, stride ldq)
+void launch_multidot(const double* Q, long long ldq, int k, const double* w, long long n, double* partial,
+                     double* out, cudaStream_t s);
+// w -= sum_j Q_j c[j]
+void launch_multiaxpy(const double* Q, long long ldq, int k, const double* c, double* w, long long n,
+                      cudaStream_t s);
+// x = sum_j c[j] Q_j
+void launch_combine(const double* Q, long long ldq, int k, const double* c, double* x, long long n, cudaStream_t s);
+// out[0] = sqrt(max(in[0], 0))
+void launch_sqrt(const double* in, double* out, cudaStream_t s);
+// y = a*x + b*y with a, b read from device scalars (nullable -> constants)
+void launch_axpby(const double* x, double* y, long long n, const double* a_dev, double a_const, double a_sign,
+                  const double* b_dev, double b_const, cudaStream_t s);
+// y = x / sqrt(*nrm2) ; returns nothing
+void launch_scale_inv_sqrt(const double* x, double* y, long long n, const double* nrm2, cudaStream_t s);
+void launch_copy(const double* x, double* y, long long n, cudaStream_t s);
+void launch_fill_uniform(double* x, long long n, uint64_t seed, uint64_t start, cudaStream_t s);
+void launch_add_scaled(const double* x, double* y, long long n, double a, cudaStream_t s);
+void launch_zero(double* x, long long n, cudaStream_t s);
+void launch_to_float(const double* x, float* y, long long n, cudaStream_t s);
+void launch_to_double(const float* x, double* y, long long n, cudaStream_t s);
+
+// ---- small dense linear algebra (one CTA per matrix) ----
+// For each matrix i: G_i (n_i x n_i at G + off_i, leading dim ld_i): in-place
+// upper Cholesky R (G = R^T R) and then Rinv = R^{-1} (written to Rinv + off_i).
+// status[i] = 0 ok, 1 non-positive pivot.
+// status[i] = 2 when a pivot R_jj^2 <= ill_cond * max_j G_jj (ill-conditioned).
+// max_n: largest n over the batch (<= 160).
+void launch_cholesky_inv(double* G, double* Rinv, const long long* off, const int* n, const int* ld, int count,
+                         int max_n, double ill_cond, int* status, cudaStream_t s);
+// Gram-Schmidt QR (two passes per column) with deterministic completion of
+// dependent columns; one CTA per column-major sector matrix (n <= 256).
+void launch_cgs2_qr(double* X, const long long* xoff, const int* rows, const int* cols, int count, double* R,
+                    const long long* roff, int ldr, double dep_tol, double accept, cudaStream_t s);
+
+// Lowest eigenpair of the symmetric tridiagonal (alpha[0..k), beta[0..k-1)).
+// out[0] = theta, out[1] = |beta_k * s_k| (residual estimate), s[0..k) the
+// eigenvector with s[0] >= 0.  beta[k-1] is the trailing coupling.
+void launch_tridiag_lowest(const double* alpha, const double* beta, int k, double* out, double* svec,
+                           cudaStream_t s);
+
+}  // namespace qed

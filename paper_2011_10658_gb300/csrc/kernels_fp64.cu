@@ -1,0 +1,577 @@
+// FP64 SIMT kernels: grouped K-concatenated GEMM with optional row gathers,
+// Lanczos vector reductions, per-sector Cholesky, tridiagonal eigensolver.
+// GB300's FP64 rate is a small fraction of its tensor throughput, so these
+// kernels are simple register-tiled DFMA loops; the mixed-precision path
+// replaces the hot contraction with tensor-core kernels.
+#include <cstdio>
+
+#include "kernels.cuh"
+
+namespace qed {
+
+namespace {
+
+constexpr int BK = 16;
+constexpr int THREADS = 256;
+
+// Row maps are sign-encoded: -1 = zero row, otherwise (row << 1) | negate.
+__device__ __forceinline__ double load_a(const KChunk& c, int m, int k) {
+  long long row = m;
+  double scale = 1.0;
+  if (c.amap) {
+    int r = c.amap[m];
+    if (r < 0) return 0.0;
+    row = r >> 1;
+    if (r & 1) scale = -1.0;
+  }
+  if (c.aval) scale *= c.aval[m];
+  return scale * c.A[row * c.a_m + (long long)k * c.a_k];
+}
+
+__device__ __forceinline__ double load_b(const KChunk& c, int k, int n) {
+  long long row = k;
+  double scale = 1.0;
+  if (c.bmap) {
+    int r = c.bmap[k];
+    if (r < 0) return 0.0;
+    row = r >> 1;
+    if (r & 1) scale = -1.0;
+  }
+  if (c.bval) scale *= c.bval[k];
+  return scale * c.B[row * c.b_k + (long long)n * c.b_n];
+}
+
+__global__ void __launch_bounds__(THREADS) kc_gemm_kernel(const KTile* __restrict__ tiles,
+                                                           const KOutput* __restrict__ outs,
+                                                           const KChunk* __restrict__ chunks,
+                                                           double* __restrict__ scratch) {
+  __shared__ double As[BK][KT_BM + 1];
+  __shared__ double Bs[BK][KT_BN + 1];
+  const KTile tile = tiles[blockIdx.x];
+  const KOutput out = outs[tile.out];
+  const int tid = threadIdx.x;
+  // each thread owns a 2x2 micro tile: rows ty*2.., cols tx*2..
+  const int tx = tid % 16, ty = tid / 16;
+  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int ci = tile.chunk_begin; ci < tile.chunk_end; ++ci) {
+    const KChunk c = chunks[ci];
+    if (c.add) {
+      // C[m,n] += alpha * A[m,n]
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+          int m = tile.m0 + ty * 2 + i, n = tile.n0 + tx * 2 + j;
+          if (m < out.M && n < out.N) acc[i][j] += c.alpha * load_a(c, m, n);
+        }
+      continue;
+    }
+    for (int k0 = 0; k0 < c.K; k0 += BK) {
+      // load A tile (32 x 16) and B tile (16 x 32): 512 elements each, 2 per thread
+      for (int e = tid; e < KT_BM * BK; e += THREADS) {
+        int mm = e / BK, kk = e % BK;
+        int m = tile.m0 + mm, k = k0 + kk;
+        As[kk][mm] = (m < out.M && k < c.K) ? c.alpha * load_a(c, m, k) : 0.0;
+      }
+      for (int e = tid; e < KT_BN * BK; e += THREADS) {
+        int kk = e / KT_BN, nn = e % KT_BN;
+        int n = tile.n0 + nn, k = k0 + kk;
+        Bs[kk][nn] = (n < out.N && k < c.K) ? load_b(c, k, n) : 0.0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        double a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
+        double b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
+        acc[0][0] = fma(a0, b0, acc[0][0]);
+        acc[0][1] = fma(a0, b1, acc[0][1]);
+        acc[1][0] = fma(a1, b0, acc[1][0]);
+        acc[1][1] = fma(a1, b1, acc[1][1]);
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      int m = tile.m0 + ty * 2 + i, n = tile.n0 + tx * 2 + j;
+      if (m >= out.M || n >= out.N) continue;
+      if (tile.part >= 0) {
+        scratch[out.part_off + (long long)tile.part * out.M * out.N + (long long)m * out.N + n] = acc[i][j];
+      } else {
+        double* p = out.C + (long long)m * out.c_m + (long long)n * out.c_n;
+        *p = out.accumulate ? (*p + acc[i][j]) : acc[i][j];
+      }
+    }
+}
+
+__global__ void kc_reduce_kernel(const KOutput* __restrict__ outs, const int* __restrict__ red_list,
+                                 const double* __restrict__ scratch) {
+  const KOutput out = outs[red_list[blockIdx.y]];
+  const long long mn = (long long)out.M * out.N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < mn; e += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int p = 0; p < out.n_parts; ++p) s += scratch[out.part_off + p * mn + e];
+    int m = (int)(e / out.N), n = (int)(e % out.N);
+    double* c = out.C + (long long)m * out.c_m + (long long)n * out.c_n;
+    *c = out.accumulate ? (*c + s) : s;
+  }
+}
+
+// ------------------------------------------------------------ reductions
+constexpr int RED_THREADS = 256;
+constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sh[RED_THREADS / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x < 32) {
+    r = threadIdx.x < RED_THREADS / 32 ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  }
+  return r;   // valid in thread 0
+}
+
+__global__ void dot_partial_kernel(const double* __restrict__ x, const double* __restrict__ y, long long n,
+                                   double* __restrict__ partial) {
+  double v = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    v = fma(x[i], y[i], v);
+  v = block_sum(v);
+  if (threadIdx.x == 0) partial[blockIdx.x] = v;
+}
+
+__global__ void finish_kernel(const double* __restrict__ partial, int count, int stride, double* __restrict__ out) {
+  // blockIdx.x selects which vector of partials (multidot)
+  double v = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) v += partial[(long long)blockIdx.x * stride + i];
+  v = block_sum(v);
+  if (threadIdx.x == 0) out[blockIdx.x] = v;
+}
+
+__global__ void multidot_partial_kernel(const double* __restrict__ Q, long long ldq, int k,
+                                        const double* __restrict__ w, long long n, double* __restrict__ partial) {
+  // blockIdx.y = column j
+  const int j = blockIdx.y;
+  const double* q = Q + (long long)j * ldq;
+  double v = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    v = fma(q[i], w[i], v);
+  v = block_sum(v);
+  if (threadIdx.x == 0) partial[(long long)j * gridDim.x + blockIdx.x] = v;
+}
+
+__global__ void multiaxpy_kernel(const double* __restrict__ Q, long long ldq, int k, const double* __restrict__ c,
+                                 double* __restrict__ w, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double v = w[i];
+    for (int j = 0; j < k; ++j) v = fma(-c[j], Q[(long long)j * ldq + i], v);
+    w[i] = v;
+  }
+}
+
+__global__ void combine_kernel(const double* __restrict__ Q, long long ldq, int k, const double* __restrict__ c,
+                               double* __restrict__ x, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int j = 0; j < k; ++j) v = fma(c[j], Q[(long long)j * ldq + i], v);
+    x[i] = v;
+  }
+}
+
+__global__ void sqrt_kernel(const double* in, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) out[0] = sqrt(fmax(in[0], 0.0));
+}
+
+__global__ void axpby_kernel(const double* __restrict__ x, double* __restrict__ y, long long n, const double* a_dev,
+                             double a_const, double a_sign, const double* b_dev, double b_const) {
+  const double a = a_sign * (a_dev ? *a_dev : a_const);
+  const double b = b_dev ? *b_dev : b_const;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = fma(a, x[i], b * y[i]);
+}
+
+__global__ void scale_inv_sqrt_kernel(const double* __restrict__ x, double* __restrict__ y, long long n,
+                                      const double* nrm2) {
+  const double inv = 1.0 / sqrt(*nrm2);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = x[i] * inv;
+}
+
+__global__ void copy_kernel(const double* __restrict__ x, double* __restrict__ y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = x[i];
+}
+
+__global__ void add_scaled_kernel(const double* __restrict__ x, double* __restrict__ y, long long n, double a) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = fma(a, x[i], y[i]);
+}
+
+__global__ void zero_kernel(double* __restrict__ x, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] = 0.0;
+}
+
+__global__ void to_float_kernel(const double* __restrict__ x, float* __restrict__ y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+
+__global__ void to_double_kernel(const float* __restrict__ x, double* __restrict__ y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (double)x[i];
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014), counter form: output i (1-based)
+// is mix(seed + i * gamma); value 2 * (x >> 11) * 2^-53 - 1.
+__global__ void fill_uniform_kernel(double* __restrict__ x, long long n, uint64_t seed, uint64_t start) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    uint64_t z = seed + (start + (uint64_t)i + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    x[i] = 2.0 * (double)(z >> 11) * 0x1.0p-53 - 1.0;
+  }
+}
+
+// Upper Cholesky G = R^T R in shared memory, then R^{-1} by back substitution.
+// One CTA per matrix; n <= 256.
+__global__ void cholesky_inv_kernel(double* G, double* Rinv, const long long* off, const int* nn, const int* ldd,
+                                    int* status, double ill_cond) {
+  extern __shared__ double sh[];
+  const int idx = blockIdx.x;
+  const int n = nn[idx], ld = ldd[idx];
+  double* g = G + off[idx];
+  double* ri = Rinv + off[idx];
+  double* R = sh;                // n x n
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) R[e] = g[(e / n) * ld + (e % n)];
+  __syncthreads();
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  // largest original diagonal = squared largest column norm of the factored matrix
+  __shared__ double gmax;
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int j = 0; j < n; ++j) mx = fmax(mx, R[j * n + j]);
+    gmax = mx;
+  }
+  __syncthreads();
+  // right-looking: for column j, R[j][j] = sqrt(G[j][j]), R[j][i] = G[j][i]/R[j][j], trailing update
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      double d = R[j * n + j];
+      if (!(d > 0.0)) { bad = 1; d = 1.0; }
+      else if (d <= ill_cond * gmax) bad = bad ? bad : 2;
+      R[j * n + j] = sqrt(d);
+    }
+    __syncthreads();
+    const double rjj = R[j * n + j];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) R[j * n + i] /= rjj;
+    __syncthreads();
+    for (int e = threadIdx.x; e < (n - j - 1) * (n - j - 1); e += blockDim.x) {
+      int a = j + 1 + e / (n - j - 1), b = j + 1 + e % (n - j - 1);
+      if (b >= a) R[a * n + b] -= R[j * n + a] * R[j * n + b];
+    }
+    __syncthreads();
+  }
+  // write R (upper) back to G, zero below
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    int a = e / n, b = e % n;
+    g[a * ld + b] = b >= a ? R[e] : 0.0;
+  }
+  __syncthreads();
+  // Rinv: solve R X = I column by column (thread per column)
+  for (int col = threadIdx.x; col < n; col += blockDim.x) {
+    for (int a = n - 1; a >= 0; --a) {
+      double v = (a == col) ? 1.0 : 0.0;
+      for (int b = a + 1; b <= col; ++b) v -= R[a * n + b] * ri[b * ld + col];
+      ri[a * ld + col] = (a <= col) ? v / R[a * n + a] : 0.0;
+    }
+    for (int a = col + 1; a < n; ++a) ri[a * ld + col] = 0.0;
+  }
+  if (threadIdx.x == 0) status[idx] = bad;
+}
+
+
+// Classical Gram-Schmidt applied twice per column, one CTA per sector matrix
+// (column-major m x n at X + xoff, Q written in place, R (n x n) at
+// R + roff with leading dimension ldr).  A column whose remainder is at
+// most dep_tol * (largest column norm) is dependent: R_jj = 0 and q_j is
+// the first unit vector e_k (k increasing, never reused) whose remainder
+// after two projections exceeds accept.
+constexpr int QR_THREADS = 1024;
+
+__device__ double cta_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    double r = l < (int)(blockDim.x / 32) ? red[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    if (l == 0) red[32] = r;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// c[i] = <q_i, v> for i < j (warp per i), then v -= sum_i c[i] q_i.
+__device__ void project_out(const double* X, long long m, int j, double* v, double* c, double* Rcol) {
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32, nw = blockDim.x / 32;
+  for (int i = w; i < j; i += nw) {
+    const double* q = X + (long long)i * m;
+    double acc = 0.0;
+    for (long long r = l; r < m; r += 32) acc = fma(q[r], v[r], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (l == 0) c[i] = acc;
+  }
+  __syncthreads();
+  for (long long r = threadIdx.x; r < m; r += blockDim.x) {
+    double a = v[r];
+    for (int i = 0; i < j; ++i) a = fma(-c[i], X[(long long)i * m + r], a);
+    v[r] = a;
+  }
+  if (Rcol)
+    for (int i = threadIdx.x; i < j; i += blockDim.x) Rcol[i] += c[i];
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(QR_THREADS) cgs2_qr_kernel(double* X, const long long* xoff, const int* rows,
+                                                              const int* cols, double* R, const long long* roff,
+                                                              int ldr, double dep_tol, double accept) {
+  __shared__ double red[40];
+  __shared__ double c[256];
+  __shared__ double rcol[256];
+  const int sidx = blockIdx.x;
+  const long long m = rows[sidx];
+  const int n = cols[sidx];
+  double* x = X + xoff[sidx];
+  double* Rs = R + roff[sidx];
+  double scale = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double acc = 0.0;
+    for (long long r = threadIdx.x; r < m; r += blockDim.x) acc = fma(x[j * m + r], x[j * m + r], acc);
+    scale = fmax(scale, sqrt(cta_sum(acc, red)));
+  }
+  long long next_k = 0;
+  for (int j = 0; j < n; ++j) {
+    double* v = x + (long long)j * m;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) rcol[i] = 0.0;
+    __syncthreads();
+    project_out(x, m, j, v, c, rcol);
+    project_out(x, m, j, v, c, rcol);
+    double acc = 0.0;
+    for (long long r = threadIdx.x; r < m; r += blockDim.x) acc = fma(v[r], v[r], acc);
+    const double nv = sqrt(cta_sum(acc, red));
+    if (nv > dep_tol * scale) {
+      const double inv = 1.0 / nv;
+      for (long long r = threadIdx.x; r < m; r += blockDim.x) v[r] *= inv;
+      if (threadIdx.x == 0) rcol[j] = nv;
+    } else {
+      if (threadIdx.x == 0) rcol[j] = 0.0;
+      // completion by unit vectors
+      for (; next_k < m; ++next_k) {
+        for (long long r = threadIdx.x; r < m; r += blockDim.x) v[r] = (r == next_k) ? 1.0 : 0.0;
+        __syncthreads();
+        project_out(x, m, j, v, c, nullptr);
+        project_out(x, m, j, v, c, nullptr);
+        double a2 = 0.0;
+        for (long long r = threadIdx.x; r < m; r += blockDim.x) a2 = fma(v[r], v[r], a2);
+        const double nw = sqrt(cta_sum(a2, red));
+        if (nw > accept) {
+          const double inv = 1.0 / nw;
+          for (long long r = threadIdx.x; r < m; r += blockDim.x) v[r] *= inv;
+          ++next_k;
+          break;
+        }
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) Rs[(long long)i * ldr + j] = i <= j ? rcol[i] : 0.0;
+    __syncthreads();
+  }
+}
+
+// Sturm-sequence count of eigenvalues below x for the tridiagonal.
+__device__ int sturm_count(const double* a, const double* b, int k, double x) {
+  int cnt = 0;
+  double d = 1.0;
+  for (int i = 0; i < k; ++i) {
+    double bb = i > 0 ? b[i - 1] * b[i - 1] : 0.0;
+    d = (a[i] - x) - (i > 0 ? bb / d : 0.0);
+    if (d == 0.0) d = -1e-300;
+    if (d < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+// Lowest eigenpair by bisection (Sturm counts) and two steps of inverse
+// iteration with a tridiagonal LU (Thomas algorithm).  Single thread.
+__global__ void tridiag_lowest_kernel(const double* alpha, const double* beta, int k, double* out, double* s) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < k; ++i) {
+    double r = (i > 0 ? fabs(beta[i - 1]) : 0.0) + (i < k - 1 ? fabs(beta[i]) : 0.0);
+    lo = fmin(lo, alpha[i] - r);
+    hi = fmax(hi, alpha[i] + r);
+  }
+  double span = hi - lo;
+  lo -= 1e-12 * fabs(span) + 1e-300;
+  hi += 1e-12 * fabs(span) + 1e-300;
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (sturm_count(alpha, beta, k, mid) >= 1) hi = mid;
+    else lo = mid;
+  }
+  const double theta = 0.5 * (lo + hi);
+  // inverse iteration on (T - shift I) with shift slightly below theta
+  double scale = fmax(fabs(lo), fabs(hi));
+  double shift = theta - 1e-13 * fmax(scale, 1e-300) - 1e-300;
+  double x[128], cp[128], dp[128];
+  for (int i = 0; i < k; ++i) x[i] = 1.0;
+  for (int iter = 0; iter < 3; ++iter) {
+    // Thomas: sub = beta[i-1], diag = alpha[i]-shift, sup = beta[i]
+    double denom = alpha[0] - shift;
+    if (denom == 0.0) denom = 1e-300;
+    cp[0] = (k > 1 ? beta[0] : 0.0) / denom;
+    dp[0] = x[0] / denom;
+    for (int i = 1; i < k; ++i) {
+      double m = (alpha[i] - shift) - beta[i - 1] * cp[i - 1];
+      if (m == 0.0) m = 1e-300;
+      cp[i] = (i < k - 1 ? beta[i] : 0.0) / m;
+      dp[i] = (x[i] - beta[i - 1] * dp[i - 1]) / m;
+    }
+    x[k - 1] = dp[k - 1];
+    for (int i = k - 2; i >= 0; --i) x[i] = dp[i] - cp[i] * x[i + 1];
+    double nrm = 0.0;
+    for (int i = 0; i < k; ++i) nrm += x[i] * x[i];
+    nrm = sqrt(nrm);
+    for (int i = 0; i < k; ++i) x[i] /= nrm;
+  }
+  const double sgn = x[0] < 0.0 ? -1.0 : 1.0;
+  for (int i = 0; i < k; ++i) s[i] = sgn * x[i];
+  // Rayleigh quotient of the tridiagonal (more accurate than the bisection midpoint)
+  double rq = 0.0;
+  for (int i = 0; i < k; ++i) {
+    double v = alpha[i] * s[i];
+    if (i > 0) v += beta[i - 1] * s[i - 1];
+    if (i < k - 1) v += beta[i] * s[i + 1];
+    rq += s[i] * v;
+  }
+  out[0] = rq;
+  out[1] = fabs(beta[k - 1] * s[k - 1]);
+}
+
+int grid_for(long long n) {
+  long long g = (n + 255) / 256;
+  if (g > 152 * 8) g = 152 * 8;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+void launch_kc_gemm(const KTile* tiles, int n_tiles, const KOutput* outs, const KChunk* chunks, double* scratch,
+                    cudaStream_t s) {
+  if (n_tiles <= 0) return;
+  kc_gemm_kernel<<<n_tiles, THREADS, 0, s>>>(tiles, outs, chunks, scratch);
+}
+
+void launch_kc_reduce(const KOutput* outs, int n_outs, const int* red_list, int n_red, double* scratch,
+                      cudaStream_t s) {
+  if (n_red <= 0) return;
+  dim3 grid(8, n_red);
+  kc_reduce_kernel<<<grid, 256, 0, s>>>(outs, red_list, scratch);
+}
+
+void launch_dot(const double* x, const double* y, long long n, double* partial, double* out, cudaStream_t s) {
+  dot_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(x, y, n, partial);
+  finish_kernel<<<1, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, RED_BLOCKS, out);
+}
+
+void launch_multidot(const double* Q, long long ldq, int k, const double* w, long long n, double* partial,
+                     double* out, cudaStream_t s) {
+  if (k <= 0) return;
+  dim3 grid(RED_BLOCKS, k);
+  multidot_partial_kernel<<<grid, RED_THREADS, 0, s>>>(Q, ldq, k, w, n, partial);
+  finish_kernel<<<k, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, RED_BLOCKS, out);
+}
+
+void launch_multiaxpy(const double* Q, long long ldq, int k, const double* c, double* w, long long n,
+                      cudaStream_t s) {
+  if (k <= 0) return;
+  multiaxpy_kernel<<<grid_for(n), 256, 0, s>>>(Q, ldq, k, c, w, n);
+}
+
+void launch_combine(const double* Q, long long ldq, int k, const double* c, double* x, long long n,
+                    cudaStream_t s) {
+  combine_kernel<<<grid_for(n), 256, 0, s>>>(Q, ldq, k, c, x, n);
+}
+
+void launch_sqrt(const double* in, double* out, cudaStream_t s) { sqrt_kernel<<<1, 32, 0, s>>>(in, out); }
+
+void launch_axpby(const double* x, double* y, long long n, const double* a_dev, double a_const, double a_sign,
+                  const double* b_dev, double b_const, cudaStream_t s) {
+  axpby_kernel<<<grid_for(n), 256, 0, s>>>(x, y, n, a_dev, a_const, a_sign, b_dev, b_const);
+}
+
+void launch_scale_inv_sqrt(const double* x, double* y, long long n, const double* nrm2, cudaStream_t s) {
+  scale_inv_sqrt_kernel<<<grid_for(n), 256, 0, s>>>(x, y, n, nrm2);
+}
+
+void launch_copy(const double* x, double* y, long long n, cudaStream_t s) {
+  copy_kernel<<<grid_for(n), 256, 0, s>>>(x, y, n);
+}
+
+void launch_fill_uniform(double* x, long long n, uint64_t seed, uint64_t start, cudaStream_t s) {
+  if (n <= 0) return;
+  fill_uniform_kernel<<<grid_for(n), 256, 0, s>>>(x, n, seed, start);
+}
+
+void launch_add_scaled(const double* x, double* y, long long n, double a, cudaStream_t s) {
+  add_scaled_kernel<<<grid_for(n), 256, 0, s>>>(x, y, n, a);
+}
+
+void launch_zero(double* x, long long n, cudaStream_t s) {
+  if (n <= 0) return;
+  zero_kernel<<<grid_for(n), 256, 0, s>>>(x, n);
+}
+
+void launch_to_float(const double* x, float* y, long long n, cudaStream_t s) {
+  to_float_kernel<<<grid_for(n), 256, 0, s>>>(x, y, n);
+}
+
+void launch_to_double(const float* x, double* y, long long n, cudaStream_t s) {
+  to_double_kernel<<<grid_for(n), 256, 0, s>>>(x, y, n);
+}
+
+void launch_cholesky_inv(double* G, double* Rinv, const long long* off, const int* n, const int* ld, int count,
+                         int max_n, double ill_cond, int* status, cudaStream_t s) {
+  if (count <= 0) return;
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(cholesky_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 160 * 8);
+    configured = true;
+  }
+  cholesky_inv_kernel<<<count, 256, (size_t)max_n * max_n * sizeof(double), s>>>(G, Rinv, off, n, ld, status,
+                                                                                  ill_cond);
+}
+
+void launch_cgs2_qr(double* X, const long long* xoff, const int* rows, const int* cols, int count, double* R,
+                    const long long* roff, int ldr, double dep_tol, double accept, cudaStream_t s) {
+  if (count <= 0) return;
+  cgs2_qr_kernel<<<count, QR_THREADS, 0, s>>>(X, xoff, rows, cols, R, roff, ldr, dep_tol, accept);
+}
+
+void launch_tridiag_lowest(const double* alpha, const double* beta, int k, double* out, double* s,
+                           cudaStream_t st) {
+  tridiag_lowest_kernel<<<1, 32, 0, st>>>(alpha, beta, k, out, s);
+}
+
+}  // namespace qed

@@ -3,6 +3,9 @@ import sys
 
 import pytest
 
+# Native plans are range-checked on the host before every launch in tests.
+os.environ.setdefault("QED_VALIDATE", "1")
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)

@@ -1,0 +1,140 @@
+"""GPU parity of the native FP64 path against the oracle, through the C ABI.
+
+Covers: seeded isometric initialisation (SplitMix64 on the device +
+CholeskyQR2 against the oracle's Householder QR), H_eff x at the root and
+after centre moves (renormalized and environment operators), single-node and
+full sweeps, energies by coupling class and observables."""
+import numpy as np
+import pytest
+
+from oracle import ed, model as omodel, ttn as ottn
+
+from ttn_layout import from_layout, to_layout
+
+pytestmark = pytest.mark.gpu
+
+REL_FP64 = 1e-10
+
+
+@pytest.fixture(scope="module")
+def q():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2011_10658_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def make_pair(q, L, chi, seed, **kw):
+    p = omodel.Params(*L, **kw)
+    ref = ottn.TTN(p, chi, seed)
+    m = q.Model(*L, **kw)
+    s = q.TTN(m, chi, seed=seed, precision="fp64")
+    return p, ref, m, s
+
+
+def max_rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(1e-300, np.max(np.abs(b))))
+
+
+CASES = [((2, 1, 1), 8, 0, {}), ((2, 2, 1), 12, 3, dict(t=0.8, m=0.3, ge2=1.5, cB=0.9, nu=20.0, Q=1)),
+         ((2, 2, 2), 8, 0, dict(t=1.0, m=1.0, ge2=1.0, cB=0.5, nu=10.0, Q=0))]
+
+
+@pytest.fixture(scope="module", params=CASES, ids=["2x1x1", "2x2x1", "2x2x2"])
+def pair(request, q):
+    L, chi, seed, kw = request.param
+    return make_pair(q, L, chi, seed, **kw)
+
+
+def test_initial_tensors(pair):
+    p, ref, m, s = pair
+    for idx in range(len(ref.nodes)):
+        got = s.node_export(idx)
+        want = to_layout(ref.T[idx], ref.labels[idx])
+        assert got.shape == want.shape
+        np.testing.assert_allclose(got, want, atol=1e-12, rtol=0)
+
+
+def test_heff_at_root(pair):
+    p, ref, m, s = pair
+    root = len(ref.nodes) - 1
+    assert s.info()["center"] == root
+    rng = np.random.default_rng(11)
+    n = s.node_size(root)
+    x = rng.standard_normal(n)
+    y = s.apply_heff(x)
+    X = from_layout(x, ref.labels[root], ref.T[root].shape)
+    want = to_layout(ref.heff_apply(root, X), ref.labels[root])
+    assert max_rel(y, want) < 1e-12
+
+
+def test_heff_after_moves(pair):
+    p, ref, m, s = pair
+    rng = np.random.default_rng(12)
+    for target in range(len(ref.nodes)):
+        ref.move_to(target)
+        s.move_center(target)
+        for idx in range(len(ref.nodes)):
+            np.testing.assert_allclose(s.node_export(idx), to_layout(ref.T[idx], ref.labels[idx]), atol=1e-11,
+                                       rtol=0)
+        n = s.node_size(target)
+        x = rng.standard_normal(n)
+        y = s.apply_heff(x)
+        X = from_layout(x, ref.labels[target], ref.T[target].shape)
+        want = to_layout(ref.heff_apply(target, X), ref.labels[target])
+        assert max_rel(y, want) < 1e-11, target
+
+
+def test_single_node_closed_form(q):
+    m = q.Model(2, 1, 1, t=1.0, m=1.0, ge2=1.0, cB=0.5, nu=10.0, Q=0)
+    s = q.TTN(m, 8, seed=0)
+    st = s.sweep(1, tol=1e-12, max_krylov=64)
+    exact = 0.25 - np.sqrt(41.0) / 4.0
+    assert abs(st["energy"] - exact) < REL_FP64 * abs(exact)
+
+
+def test_sweep_2x2x1_reaches_ed(q):
+    kw = dict(t=1.0, m=1.0, ge2=1.0, cB=0.5, nu=10.0, Q=0)
+    m = q.Model(2, 2, 1, **kw)
+    s = q.TTN(m, 12, seed=0)
+    st = s.sweep(1, tol=1e-12, max_krylov=64)
+    e_ed = ed.config_ed(omodel.Params(2, 2, 1, **kw))
+    assert abs(st["energy"] - e_ed) < 1e-9 * abs(e_ed)
+    et, ew, parts = s.energy()
+    assert abs(et - st["energy"]) < 1e-9 * abs(e_ed)
+    assert abs(sum(parts.values()) - et) < 1e-10 * abs(et)
+    sc = s.measure("scalars")
+    assert abs(sc[2] - 0.0) < 1e-10
+
+
+def test_sweep_matches_oracle_node_by_node(pair):
+    p, ref, m, s = pair
+    ref_e = []
+    got_e = []
+    for idx in range(len(ref.nodes)):
+        ref_e.append(ref.optimize_node(idx, tol=1e-12))
+        got_e.append(s.optimize_node(idx, tol=1e-12, max_krylov=64))
+    ref_e, got_e = np.array(ref_e), np.array(got_e)
+    assert np.max(np.abs(got_e - ref_e) / np.abs(ref_e)) < REL_FP64, (got_e, ref_e)
+
+
+def test_energy_classes_and_observables(pair):
+    p, ref, m, s = pair
+    # after the node-by-node sweep of the previous test, both states agree
+    et, ew, parts = s.energy()
+    want_total = ottn.expectation(ref, p)
+    assert abs(et - want_total) < REL_FP64 * abs(want_total)
+    for c in ("t", "m", "ge2", "cB", "nu"):
+        want = ottn.expectation(ref, omodel.class_only(p, c))
+        assert abs(parts[c] - want) < 1e-9 * max(1.0, abs(want_total)), c
+    assert abs(ew - (et - parts["nu"])) < 1e-12 * abs(et)
+    obs = ref.observables()
+    sc = s.measure("scalars")
+    assert abs(sc[0] - obs["rho"]) < 1e-9
+    assert abs(sc[1] - obs["delta_L"]) < 1e-8
+    assert abs(sc[2] - p.Q) < 1e-10
+    np.testing.assert_allclose(s.measure("phi"), obs["phi"], atol=1e-9)
+    np.testing.assert_allclose(s.measure("elink"), obs["E_link"], atol=1e-9)
+    np.testing.assert_allclose(s.measure("sigma"), obs["sigma"], atol=1e-9)

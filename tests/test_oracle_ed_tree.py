@@ -183,3 +183,35 @@ def test_qr_positive():
     np.testing.assert_allclose(Qm @ R, A, atol=1e-13)
     np.testing.assert_allclose(Qm.T @ Qm, np.eye(7), atol=1e-13)
     assert np.allclose(np.tril(R, -1), 0)
+
+
+def test_qr_sector_full_rank_equals_householder():
+    rng = np.random.default_rng(3)
+    for m, n in ((50, 7), (9, 9), (300, 32)):
+        A = rng.standard_normal((m, n))
+        Q1, R1 = tree.qr_positive(A)
+        Q2, R2 = tree.qr_gram_schmidt(A)
+        np.testing.assert_allclose(Q2, Q1, atol=1e-12)
+        np.testing.assert_allclose(R2, R1, atol=1e-12)
+        Q3, R3 = tree.qr_sector(A)
+        np.testing.assert_array_equal(Q3, Q1)
+
+
+def test_qr_sector_rank_deficient():
+    # hand example: second column zero -> R_11 = 0, q_1 completed by e_1
+    X = np.array([[2.0, 0.0], [0.0, 0.0], [0.0, 0.0]])
+    Q, R = tree.qr_sector(X)
+    np.testing.assert_array_equal(Q, np.array([[1.0, 0.0], [0.0, 1.0], [0.0, 0.0]]))
+    np.testing.assert_array_equal(R, np.array([[2.0, 0.0], [0.0, 0.0]]))
+    # general: rank 3 of 6 columns, noise far below the dependency threshold
+    rng = np.random.default_rng(4)
+    B = rng.standard_normal((40, 3)) @ rng.standard_normal((3, 6))
+    B += 1e-13 * rng.standard_normal(B.shape)
+    Q, R = tree.qr_sector(B)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(6), atol=1e-12)
+    np.testing.assert_allclose(Q @ R, B, atol=1e-8)
+    assert np.allclose(np.tril(R, -1), 0)
+    assert np.all(np.diag(R) >= 0)
+    assert np.sum(np.diag(R) == 0) == 3
+    with pytest.raises(ValueError):
+        tree.qr_sector(rng.standard_normal((3, 5)))
