@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Benchmark of the TTN sweep hot path on GB300.
+
+Workload: compact lattice QED on a 4x4x4 open lattice (64 dressed sites),
+t = m = 1, g^2 = 1 (ge2 = 1, plaquette cB = 1/2, penalty nu = 10), zero net
+charge, U(1)-symmetric binary TTN with bond dimension 64, tensors from
+SplitMix64 seed 1, Lanczos tolerance 1e-6 (relative residual), Krylov 64.
+One step = one full sweep (63 node updates: centre moves with QR and
+operator updates, Lanczos with H_eff products, tensor updates).
+
+value = algorithmic H_eff x flops of every product in the timed sweeps /
+timed wall time (TFLOP/s); the same sweeps' seconds are in ms_per_step.
+Precision (default tf32x3): bottom-node products on tcgen05 with TF32
+hi/lo operand splitting and FP32 accumulation, upper nodes in FP32; Lanczos
+vectors, QR, operator updates and the final energy of each update in FP64.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (H_eff x at bottom node 0 with synthetic environment operators of
+the right shapes) and reports it in the same unit.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "TTN sweep s & H_eff·ψ TFLOP/s, mixed vs FP64 at |ΔE|/|E|≤1e-6, 4³ χ=64"
+L = (4, 4, 4)
+CHI = 64
+SEED = 1
+G2 = 1.0
+Q = 0
+TOL = 1e-6
+KRYLOV = 64
+
+
+def workload_name(prec):
+    return (f"4x4x4 open-boundary lattice QED (64 dressed sites, d=267), t=m=1, g2=1 (ge2=1, cB=0.5, nu=10), "
+            f"Q=0, TTN chi=64 U(1) blocks, seed 1, Lanczos tol 1e-6, Krylov 64, precision {prec}")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clocks and throttle reasons (200 ms)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_from_profile(kernel_src):
+    """DRAM bytes per launch of the tensor-core kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "tc_heff_4x4x4_chi64_traffic.txt")
+    try:
+        digest = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+        vals = {}
+        for line in open(path):
+            if "=" in line and not line.startswith("#"):
+                k, v = line.split("=", 1)
+                vals[k.strip()] = v.strip()
+        if vals.get("kernel_source_sha256_16") != digest:
+            return None
+        return float(vals["dram_bytes_per_launch_full_size"])
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------- oracle sample
+def oracle_sample(n_matvecs=None, budget_s=20.0):
+    """Time the FP64 oracle's H_eff x at bottom node 0 of the workload.
+    Environment operators are random matrices of the right shapes (the
+    oracle's cost depends on shapes only).  Returns (seconds per matvec,
+    matvecs timed, cores)."""
+    import numpy as np
+    from oracle import model as omodel
+    from oracle import ttn as ottn
+    c = workloads.qed_couplings(G2)
+    p = omodel.Params(*L, Q=Q, **c)
+    ref = ottn.TTN(p, CHI, SEED, build_ops=False)
+    node = 0
+    rng = np.random.default_rng(0)
+    dim = ref.T[node].shape[2]
+    env = {}
+    for k, tm in enumerate(ref.terms):
+        if ref._crosses(tm, ref.region[node]):
+            env[k] = rng.standard_normal((dim, dim))
+    H = rng.standard_normal((dim, dim))
+    env["H"] = H + H.T
+    ref.down[node] = env
+    terms = ref.heff_terms(node)
+    X = ref.T[node]
+    ref.heff_apply(node, X, terms)   # warm
+    times = []
+    t_start = time.time()
+    while True:
+        t0 = time.time()
+        ref.heff_apply(node, X, terms)
+        times.append(time.time() - t0)
+        if n_matvecs is not None and len(times) >= n_matvecs:
+            break
+        if n_matvecs is None and time.time() - t_start > budget_s:
+            break
+    try:
+        import numpy as _np
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count()
+    return float(sum(times) / len(times)), len(times), cores
+
+
+def node0_flops():
+    """Algorithmic flops of one H_eff x at bottom node 0 (the same count the
+    native profiler reports), from a short native run."""
+    import paper_2011_10658_gb300 as q
+    c = workloads.qed_couplings(G2)
+    s = q.TTN(q.Model(*L, Q=Q, **c), CHI, seed=SEED, precision="tf32x3")
+    s.move_center(0)
+    s.set_profiling(True)
+    s.reset_timing()
+    import numpy as np
+    s.apply_heff(np.ones(s.node_size(0)))
+    t = s.kernel_timing("tc_heff")
+    s.close()
+    return t["flops_alg"] / max(1, t["launches"])
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per_step = []
+    flops = None
+    try:
+        import torch
+        if torch.cuda.is_available():
+            flops = node0_flops()
+    except Exception:
+        flops = None
+    for i in range(args.warmup + args.steps):
+        t, n, cores = oracle_sample(n_matvecs=2)
+        if i >= args.warmup:
+            per_step.append(t * n)
+    sec_per_mv = sum(per_step) / (2 * len(per_step))
+    value = (flops / sec_per_mv / 1e12) if flops else None
+    sample = (f"FP64 NumPy/SciPy oracle, H_eff x at bottom node 0 of the 4x4x4 chi=64 workload (environment "
+              f"operators random, same shapes), 2 products per step, {sec_per_mv:.3f} s per product")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(per_step) / len(per_step),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload_name("fp64 CPU oracle")},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- native arm
+def run_native(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import paper_2011_10658_gb300 as q
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    c = workloads.qed_couplings(G2)
+    model = q.Model(*L, Q=Q, **c)
+    # replicas only: rank r runs an independent problem from seed SEED + r
+    s = q.TTN(model, CHI, seed=SEED + rank, precision=args.precision, stream=stream.cuda_stream)
+    s.set_profiling(True)
+    energies = []
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        st = s.sweep(1, tol=TOL, max_krylov=KRYLOV, allow_noconv=True)
+        energies.append(st["energy"])
+    s.reset_timing()
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = q.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        st = s.sweep(1, tol=TOL, max_krylov=KRYLOV, allow_noconv=True)
+        stats.append(st)
+        energies.append(st["energy"])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    launches = q.launch_count() - launches0
+    clocks = sampler.stop()
+    kt = {k: s.kernel_timing(k) for k in ("tc_heff", "heff_simt_bottom", "heff_simt_upper")}
+    flops = sum(v["flops_alg"] for v in kt.values())
+    if world > 1:
+        t = torch.tensor([elapsed_ms, flops], device="cuda", dtype=torch.float64)
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        elapsed_ms, flops = mx[0].item(), sm[1].item()
+    value = flops / (elapsed_ms * 1e-3) / 1e12
+
+    # dominant kernel roofline
+    dom = max(kt, key=lambda k: kt[k]["ms"])
+    d = kt[dom]
+    pk, src = peaks()
+    per_launch_ms = d["ms"] / max(1, d["launches"])
+    achieved = d["flops_alg"] / max(1, d["launches"]) / (per_launch_ms * 1e-3) / 1e12
+    if dom == "tc_heff":
+        # TF32 tensor rate = BF16 rate x nominal ratio (1.1 / 2.25 PFLOP/s dense); kernel timed inside a long step
+        peak = pk["bf16_tflops_sustained"] * (1.1 / 2.25)
+        bound, peak_note = "tensor", f"TF32 dense = {src} sustained BF16 {pk['bf16_tflops_sustained']} x 1.1/2.25"
+        traffic = traffic_from_profile(os.path.join(ROOT, "paper_2011_10658_gb300", "csrc", "kernels_tc.cu"))
+    else:
+        # FP32 SIMT: 152 SMs x 128 lanes x 2 flops x max SM clock
+        peak = 152 * 128 * 2 * (pk.get("sm_max_mhz", 2070.0) * 1e6) / 1e12
+        bound, peak_note, traffic = "alu", "FP32 SIMT 152 x 128 x 2 x 2070 MHz", None
+    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_note,
+                "launches": d["launches"], "ms_per_launch": per_launch_ms,
+                "algorithmic_flops_per_launch": d["flops_alg"] / max(1, d["launches"]),
+                "executed_flops_per_launch": d["flops_exec"] / max(1, d["launches"]),
+                "share_of_step": d["ms"] / elapsed_ms}
+
+    # end to end through the public API with host buffers: tensors in from
+    # pinned host memory, sweep, tensors and energy back to the host
+    nn = s.info()["n_nodes"]
+    host = [torch.empty(s.node_size(i), dtype=torch.float64, pin_memory=True) for i in range(nn)]
+    for i in range(nn):
+        host[i].numpy()[:] = s.node_export(i)
+    h2d = sum(h.numel() * 8 for h in host)
+    e2e_flops = 0.0
+    s.reset_timing()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    for _ in range(args.steps):
+        s.load_tensors([(h.data_ptr(), h.numel()) for h in host])
+        st = s.sweep(1, tol=TOL, max_krylov=KRYLOV, allow_noconv=True)
+        for i in range(nn):
+            host[i].numpy()[:] = s.node_export(i)
+        e_back = st["energy"]
+    torch.cuda.synchronize()
+    e2e_s = time.time() - t0
+    kt2 = {k: s.kernel_timing(k) for k in ("tc_heff", "heff_simt_bottom", "heff_simt_upper")}
+    e2e_flops = sum(v["flops_alg"] for v in kt2.values())
+    e2e = {"value": e2e_flops / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": h2d + 8, "seconds_per_step": e2e_s / args.steps}
+
+    # FP64 GPU path on the same workload and sweeps for |dE|/|E|
+    compare = None
+    if args.compare_fp64 and args.precision != "fp64" and rank == 0:
+        r = q.TTN(model, CHI, seed=SEED + rank, precision="fp64", stream=stream.cuda_stream)
+        e64 = []
+        t0 = time.time()
+        for _ in range(args.warmup + args.steps):
+            e64.append(r.sweep(1, tol=TOL, max_krylov=KRYLOV, allow_noconv=True)["energy"])
+        fp64_s = (time.time() - t0) / (args.warmup + args.steps)
+        rel = [abs(a - b) / abs(b) for a, b in zip(energies, e64)]
+        compare = {"energies_mixed": energies, "energies_fp64": e64, "max_rel_dE": max(rel),
+                   "fp64_seconds_per_sweep": fp64_s}
+        r.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t_mv, n_mv, cores = oracle_sample(budget_s=args.cpu_seconds)
+        f0 = node0_flops()
+        cpu = {"value": f0 / t_mv / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+               "sample": (f"FP64 NumPy/SciPy oracle: {n_mv} H_eff x products at bottom node 0 of this workload "
+                          f"(random environment operators of the same shapes), {t_mv:.3f} s each; "
+                          f"{f0 / 1e9:.2f} GFLOP algorithmic per product")}
+
+    if rank == 0:
+        total_mv = sum(st["matvecs"] for st in stats)
+        mixed_mv = sum(st["matvecs_mixed"] for st in stats)
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": workload_name(args.precision), "l2": "inputs larger than L2 (working set > 1 GB)",
+                       "parallelism": f"replicas x{world} (independent seeds)"},
+            "sweep_s": elapsed_ms / args.steps / 1e3,
+            "energy": energies[-1],
+            "matvecs_per_sweep": total_mv / args.steps, "mixed_matvecs_per_sweep": mixed_mv / args.steps,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": launches, "kernels": kt, "fp64_comparison": compare,
+        }
+        print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", default="tf32x3", choices=["fp64", "tf32", "bf16", "tf32x3"])
+    ap.add_argument("--compare-fp64", dest="compare_fp64", action="store_true", default=True)
+    ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

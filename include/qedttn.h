@@ -58,7 +58,13 @@ typedef enum {
   QED_EUNSUPPORTED = -7 /* configuration outside what this build supports */
 } qed_status;
 
-enum { QED_PREC_FP64 = 0, QED_PREC_TF32 = 1, QED_PREC_BF16 = 2 };
+/* Arithmetic of the H_eff products inside the eigensolver (Lanczos vectors,
+ * QR, operator updates and reported energies are FP64 in every mode):
+ * FP64; TF32 or BF16 tensor-core operands with FP32 accumulation; TF32X3:
+ * operands split as hi + lo TF32 parts, three products per term (about 21
+ * significant bits).  Upper (non-bottom) nodes use FP32 arithmetic in the
+ * mixed modes. */
+enum { QED_PREC_FP64 = 0, QED_PREC_TF32 = 1, QED_PREC_BF16 = 2, QED_PREC_TF32X3 = 3 };
 
 /* Local operator kinds of qed_local_op (half-link index j: 0..5 for
  * -x, -y, -z, +x, +y, +z). */
@@ -69,7 +75,8 @@ enum {
   QED_OP_C = 3,    /* eta_i^dag eta_j      (plaquette factor)  */
   QED_OP_P = 4,    /* projector on k_j = k (Eq. (16))          */
   QED_OP_N = 5,    /* psi^dag psi          (mass term)         */
-  QED_OP_E2 = 6    /* sum over mask j of (1 - k_j)^2, Eq. (10) squared; j1 = bit mask */
+  QED_OP_E2 = 6,   /* sum over mask j of (1 - k_j)^2, Eq. (10) squared; j1 = bit mask */
+  QED_OP_PC = 8    /* 1 - projector on k_j = k (penalty factor)                  */
 };
 
 typedef struct qed_model qed_model;
@@ -94,7 +101,8 @@ int qed_local_op(int parity, int op_kind, int j1, int j2, int16_t *src, double *
 int qed_model_create(const qed_params *p, qed_model **out);
 void qed_model_destroy(qed_model *m);
 /* n_sites, number of product terms, number of tree nodes, additive constant
- * nu * N_links of Eq. (16). */
+ * (zero: the penalty of Eq. (16) is written as nu sum_k P^k_x (1 -
+ * P^{2-k}_y) per link, an exact rewrite of nu (1 - delta_{2,L})). */
 int qed_model_info(const qed_model *m, int32_t *n_sites, int32_t *n_terms, int32_t *n_nodes, double *constant);
 /* Term list: for term i, coef[i], cls[i] (0 t, 1 m, 2 ge2, 3 cB, 4 nu) and up
  * to four factors ops[i][f] = (site, kind, a, b) with n_ops[i] factors. */
@@ -116,7 +124,8 @@ void ttn_destroy(ttn_state *s);
 
 typedef struct {
   double energy;            /* last eigenvalue (penalty and constant included) */
-  int32_t matvecs;          /* H_eff applications */
+  int32_t matvecs;          /* H_eff applications (all precisions) */
+  int32_t matvecs_mixed;    /* of which on the tensor-core (TF32/BF16) path */
   int32_t node_updates;
   int32_t not_converged;    /* node updates that stopped above tolerance */
   double max_rel_residual;  /* max |beta_k s_k| / |theta| */
@@ -130,6 +139,30 @@ typedef struct {
  * residual <= tol |theta|, restarted every max_krylov steps).
  * Returns QED_ENOCONV (stats still valid) if some update stopped early. */
 int ttn_sweep(ttn_state *s, int32_t n_sweeps, double tol, int32_t max_krylov, ttn_sweep_stats *out);
+/* Mixed precision (QED_PREC_TF32 / QED_PREC_BF16): bottom-node updates run
+ * Lanczos with tensor-core H_eff products until the residual reaches
+ * max(tol, mixed_tol) (or stops improving), then continue from that Ritz
+ * vector with FP64 products until the FP64 residual reaches tol.  Default
+ * mixed_tol: 1e-7 (TF32X3), 1e-5 (TF32), 1e-4 (BF16). */
+int ttn_set_mixed_tol(ttn_state *s, double mixed_tol);
+/* Last node update: FP64 and mixed Lanczos iterations, |beta s| / |theta|. */
+int ttn_last_update(ttn_state *s, int32_t *iters_fp64, int32_t *iters_mixed, double *rel_residual);
+
+/* Kernel timing with CUDA events on the state's stream (off by default).
+ * kernel_class: 0 = tensor-core bottom-node H_eff, 1 = SIMT bottom-node
+ * H_eff (FP64), 2 = SIMT upper-node H_eff (FP64, or FP32 in the
+ * low-precision phase of a mixed state), 3 = whole centre moves (QR,
+ * R absorption, operator updates), 4 = whole Lanczos calls (products
+ * included; the difference is vector work and idle time).  Returns accumulated milliseconds,
+ * launches, algorithmic flops (nonzero rows of the monomial gathers times
+ * the dense environment contraction), executed flops (padded tiles) and
+ * algorithmic bytes (staged input read, FP64 output written, operator
+ * blocks read) since the last reset. */
+int ttn_set_profiling(ttn_state *s, int on);
+int ttn_reset_timing(ttn_state *s);
+int ttn_kernel_timing(ttn_state *s, int kernel_class, double *ms, int64_t *launches, double *flops_alg,
+                      double *flops_exec, double *bytes_alg);
+
 /* Optimise one node (moving the centre there first). */
 int ttn_optimize_node(ttn_state *s, int32_t node, double tol, int32_t max_krylov, double *energy);
 /* Move the isometry centre to a node. */
@@ -163,9 +196,19 @@ int ttn_measure(ttn_state *s, int kind, double *out, int64_t cap, int64_t *n);
 int ttn_node_export(ttn_state *s, int32_t node, double *buf, int64_t cap, int64_t *n);
 /* Replace one node tensor (same layout).  QED_ENAN on non-finite input. */
 int ttn_node_import(ttn_state *s, int32_t node, const double *buf, int64_t n);
+/* Resume from host-held tensors: bufs[i] (sizes[i] elements, block layout)
+ * for every node i; the tree must be isometric towards the root (as after
+ * ttn_sweep, or ttn_node_export of such a state).  Copies them to the device
+ * (pinned host memory makes the copies asynchronous), rebuilds every
+ * renormalized operator and puts the centre at the root. */
+int ttn_load_tensors(ttn_state *s, const double *const *bufs, const int64_t *sizes, int32_t n_nodes);
+/* Kernels launched by the library in this process so far (all states). */
+int qed_launch_count(int64_t *count);
 
 /* y = H_eff x at the current centre (Methods step (i)), x and y in the
- * centre's block layout; host buffers (copied in and out). */
+ * centre's block layout; host buffers (copied in and out).  Computed in the
+ * state's precision: tensor-core TF32/BF16 products at bottom nodes of a
+ * mixed-precision state, FP64 otherwise. */
 int ttn_apply_heff(ttn_state *s, const double *x, double *y, int64_t n);
 /* Same with device buffers on the state's stream (no host copies). */
 int ttn_apply_heff_device(ttn_state *s, const double *x_device, double *y_device, int64_t n);

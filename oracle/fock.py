@@ -138,7 +138,7 @@ def fock_op(key):
 
     Keys: ('M', j) = psi^dag eta_j; ('Md', j) = eta_j^dag psi;
     ('C', i, j) = eta_i^dag eta_j; ('P', j, k) = projector on k_j = k;
-    ('n',) = psi^dag psi.  Half-link indices are 0-based (0..5 for
+    ('PC', j, k) = 1 - ('P', j, k); ('n',) = psi^dag psi.  Half-link indices are 0-based (0..5 for
     -x, -y, -z, +x, +y, +z)."""
     kind = key[0]
     if kind == "M":
@@ -157,6 +157,8 @@ def fock_op(key):
         if k == 1:
             return (na @ (one - nb)).tocsr()
         return (na @ nb).tocsr()
+    if kind == "PC":
+        return (identity() - fock_op(("P", key[1], key[2]))).tocsr()
     if kind == "n":
         return number(0)
     raise KeyError(key)

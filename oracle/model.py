@@ -14,8 +14,9 @@ Readings of the paper used here (listed in the design doc as well):
   acts on them and each costs (ge2/2)(1 - k)^2;
 * the electric energy of an internal link (x, +mu) is (ge2/2)(1 - k_{x,+mu})^2
   read on the lower site, Eq. (10);
-* the penalty of Eq. (16) is nu * N_links - nu * sum_k P^k_{x,+mu} (x)
-  P^{2-k}_{x+mu,-mu}; the constant nu * N_links is carried separately.
+* the penalty of Eq. (16), nu * (1 - delta_{2,L}) per internal link, is
+  written as nu * sum_k P^k_{x,+mu} (x) (1 - P^{2-k}_{x+mu,-mu}) (exact,
+  since sum_k P^k = 1), so no additive constant remains.
 """
 from dataclasses import dataclass, field, replace
 
@@ -163,12 +164,14 @@ def build_terms(p: Params):
         bwd = tuple((s, ("C", key[2], key[1])) for (s, key) in fwd)
         terms.append(Term(p.cB, "cB", 1.0, tuple(sorted(fwd))))
         terms.append(Term(p.cB, "cB", 1.0, tuple(sorted(bwd))))
-    # penalty nu sum (1 - delta_{2,L}) = nu N_links - nu sum_k P^k P^{2-k}, Eq. (16)
+    # penalty nu sum (1 - delta_{2,L}), Eq. (16), written with sum_k P^k = 1 as
+    # nu sum_k P^k_{x,+mu} (1 - P^{2-k}_{y,-mu}): three non-negative product
+    # terms per link and no additive constant
     links = lat.links()
     for (x, mu, y) in links:
         for k in range(3):
-            terms.append(Term(-p.nu, "nu", -1.0, ((x, ("P", plus(mu), k)), (y, ("P", minus(mu), 2 - k)))))
-    constant = p.nu * len(links)
+            terms.append(Term(p.nu, "nu", 1.0, ((x, ("P", plus(mu), k)), (y, ("PC", minus(mu), 2 - k)))))
+    constant = 0.0
     # drop exactly-zero couplings: they contribute nothing
     terms = [tm for tm in terms if tm.coef != 0.0]
     return terms, constant

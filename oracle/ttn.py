@@ -70,7 +70,7 @@ def renormalize(T, ops, out_leg):
 
 
 class TTN:
-    def __init__(self, p: _model.Params, chi, seed):
+    def __init__(self, p: _model.Params, chi, seed, build_ops=True):
         self.p = p
         self.chi = chi
         self.lat = _model.Lattice(p.Lx, p.Ly, p.Lz)
@@ -91,9 +91,10 @@ class TTN:
         self.center = n - 1
         self.up = [None] * n
         self.down = [None] * n
-        for nd in self.nodes:
-            if nd.parent >= 0:
-                self.up[nd.index] = self._up_ops(nd.index)
+        if build_ops:
+            for nd in self.nodes:
+                if nd.parent >= 0:
+                    self.up[nd.index] = self._up_ops(nd.index)
         self.energies = []
 
     # ------------------------------------------------------------ setup

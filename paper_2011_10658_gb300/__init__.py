@@ -11,14 +11,21 @@ import numpy as np
 from . import _lib
 from ._lib import QedError, QedParams, SweepStats, check, lib
 
-PREC = {"fp64": 0, "tf32": 1, "bf16": 2}
-OP = {"I": 0, "M": 1, "MD": 2, "C": 3, "P": 4, "N": 5, "E2": 6}
+PREC = {"fp64": 0, "tf32": 1, "bf16": 2, "tf32x3": 3}
+OP = {"I": 0, "M": 1, "MD": 2, "C": 3, "P": 4, "N": 5, "E2": 6, "PC": 8}
 MEAS = {"probs": 0, "phi": 1, "nx": 2, "qx": 3, "k": 4, "elink": 5, "scalars": 6, "sigma": 7}
 CLASSES = ("t", "m", "ge2", "cB", "nu")
 
 
 def _ptr(a, ctype):
     return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def launch_count():
+    """Kernels launched by libqedttn in this process."""
+    n = ctypes.c_int64()
+    check(lib().qed_launch_count(ctypes.byref(n)))
+    return n.value
 
 
 def basis(parity):
@@ -119,13 +126,36 @@ class TTN:
     def sweep(self, n=1, tol=1e-12, max_krylov=64, allow_noconv=False):
         st = SweepStats()
         check(lib().ttn_sweep(self._h, n, tol, max_krylov, ctypes.byref(st)), allow=(-4,) if allow_noconv else ())
-        return dict(energy=st.energy, matvecs=st.matvecs, node_updates=st.node_updates,
+        return dict(energy=st.energy, matvecs=st.matvecs, matvecs_mixed=st.matvecs_mixed, node_updates=st.node_updates,
                     not_converged=st.not_converged, max_rel_residual=st.max_rel_residual, seconds=st.seconds)
 
     def optimize_node(self, node, tol=1e-12, max_krylov=64):
         e = ctypes.c_double()
         check(lib().ttn_optimize_node(self._h, node, tol, max_krylov, ctypes.byref(e)))
         return e.value
+
+    def set_mixed_tol(self, tol):
+        check(lib().ttn_set_mixed_tol(self._h, tol))
+
+    def last_update(self):
+        a, b, r = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        check(lib().ttn_last_update(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(r)))
+        return dict(iters_fp64=a.value, iters_mixed=b.value, rel_residual=r.value)
+
+    def set_profiling(self, on=True):
+        check(lib().ttn_set_profiling(self._h, 1 if on else 0))
+
+    def reset_timing(self):
+        check(lib().ttn_reset_timing(self._h))
+
+    def kernel_timing(self, kernel_class):
+        ms, n, fa, fe, ba = (ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_double(),
+                             ctypes.c_double())
+        k = {"tc_heff": 0, "heff_simt_bottom": 1, "heff_simt_upper": 2, "move": 3,
+             "lanczos": 4}.get(kernel_class, kernel_class)
+        check(lib().ttn_kernel_timing(self._h, k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(fa),
+                                      ctypes.byref(fe), ctypes.byref(ba)))
+        return dict(ms=ms.value, launches=n.value, flops_alg=fa.value, flops_exec=fe.value, bytes_alg=ba.value)
 
     def move_center(self, node):
         check(lib().ttn_move_center(self._h, node))
@@ -165,6 +195,24 @@ class TTN:
     def node_import(self, node, data):
         data = np.ascontiguousarray(data, dtype=np.float64)
         check(lib().ttn_node_import(self._h, node, _ptr(data, ctypes.c_double), data.size))
+
+    def load_tensors(self, arrays):
+        """arrays: one float64 buffer per node (numpy arrays or integer host
+        pointers with sizes as (ptr, n) pairs)."""
+        n = len(arrays)
+        ptrs = (ctypes.POINTER(ctypes.c_double) * n)()
+        sizes = np.zeros(n, dtype=np.int64)
+        keep = []
+        for i, a in enumerate(arrays):
+            if isinstance(a, tuple):
+                ptrs[i] = ctypes.cast(ctypes.c_void_p(a[0]), ctypes.POINTER(ctypes.c_double))
+                sizes[i] = a[1]
+            else:
+                a = np.ascontiguousarray(a, dtype=np.float64)
+                keep.append(a)
+                ptrs[i] = _ptr(a, ctypes.c_double)
+                sizes[i] = a.size
+        check(lib().ttn_load_tensors(self._h, ptrs, _ptr(sizes, ctypes.c_int64), n))
 
     def apply_heff(self, x):
         x = np.ascontiguousarray(x, dtype=np.float64)

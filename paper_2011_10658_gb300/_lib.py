@@ -29,7 +29,7 @@ class QedParams(ctypes.Structure):
 
 
 class SweepStats(ctypes.Structure):
-    _fields_ = [("energy", c_double), ("matvecs", c_int32), ("node_updates", c_int32),
+    _fields_ = [("energy", c_double), ("matvecs", c_int32), ("matvecs_mixed", c_int32), ("node_updates", c_int32),
                 ("not_converged", c_int32), ("max_rel_residual", c_double), ("seconds", c_double)]
 
 
@@ -48,6 +48,11 @@ SIGNATURES = [
     ("ttn_destroy", None, [c_void_p]),
     ("ttn_sweep", c_int, [c_void_p, c_int32, c_double, c_int32, ctypes.POINTER(SweepStats)]),
     ("ttn_optimize_node", c_int, [c_void_p, c_int32, c_double, c_int32, c_double_p]),
+    ("ttn_set_mixed_tol", c_int, [c_void_p, c_double]),
+    ("ttn_last_update", c_int, [c_void_p, c_int32_p, c_int32_p, c_double_p]),
+    ("ttn_set_profiling", c_int, [c_void_p, c_int]),
+    ("ttn_reset_timing", c_int, [c_void_p]),
+    ("ttn_kernel_timing", c_int, [c_void_p, c_int, c_double_p, c_int64_p, c_double_p, c_double_p, c_double_p]),
     ("ttn_move_center", c_int, [c_void_p, c_int32]),
     ("ttn_info", c_int, [c_void_p, c_int32_p, c_int32_p, c_int64_p]),
     ("ttn_node_size", c_int, [c_void_p, c_int32, c_int64_p]),
@@ -55,6 +60,8 @@ SIGNATURES = [
     ("ttn_measure", c_int, [c_void_p, c_int, c_double_p, c_int64, c_int64_p]),
     ("ttn_node_export", c_int, [c_void_p, c_int32, c_double_p, c_int64, c_int64_p]),
     ("ttn_node_import", c_int, [c_void_p, c_int32, c_double_p, c_int64]),
+    ("ttn_load_tensors", c_int, [c_void_p, ctypes.POINTER(c_double_p), c_int64_p, c_int32]),
+    ("qed_launch_count", c_int, [c_int64_p]),
     ("ttn_apply_heff", c_int, [c_void_p, c_double_p, c_double_p, c_int64]),
     ("ttn_apply_heff_device", c_int, [c_void_p, c_void_p, c_void_p, c_int64]),
 ]

@@ -24,6 +24,7 @@ int engine_status(qed::Engine* e, int rc) {
   if (rc == -2) return QED_ENOMEM;
   if (rc == -5) return QED_ENAN;
   if (rc == -7) return QED_EUNSUPPORTED;
+  if (rc == -6) return QED_ETIMEOUT;
   if (rc == -1) return QED_EINVAL;
   return QED_ECUDA;
 }
@@ -70,10 +71,11 @@ QED_API int qed_basis(int parity, int8_t* table, int32_t* n_rows) {
 QED_API int qed_local_op(int parity, int op_kind, int j1, int j2, int16_t* src, double* val) {
   if (parity != 1 && parity != -1) return fail(QED_EINVAL, "parity must be +1 or -1");
   if (!src || !val) return fail(QED_EINVAL, "null output");
-  if (op_kind < QED_OP_IDENTITY || op_kind > QED_OP_E2) return fail(QED_EINVAL, "unknown op kind");
+  if (op_kind < QED_OP_IDENTITY || (op_kind > QED_OP_E2 && op_kind != QED_OP_PC))
+    return fail(QED_EINVAL, "unknown op kind");
   if (op_kind != QED_OP_E2 && (j1 < 0 || j1 > 5)) return fail(QED_EINVAL, "half-link index out of range");
   if (op_kind == QED_OP_C && (j2 < 0 || j2 > 5 || j1 == j2)) return fail(QED_EINVAL, "C needs two distinct half-links");
-  if (op_kind == QED_OP_P && (j2 < 0 || j2 > 2)) return fail(QED_EINVAL, "P needs k in 0..2");
+  if ((op_kind == QED_OP_P || op_kind == QED_OP_PC) && (j2 < 0 || j2 > 2)) return fail(QED_EINVAL, "P needs k in 0..2");
   if (op_kind == QED_OP_E2 && (j1 < 0 || j1 > 63)) return fail(QED_EINVAL, "E2 mask out of range");
   QED_TRY(
     qed::OpKey k;
@@ -184,7 +186,8 @@ QED_API int ttn_create(const qed_model* m, int32_t chi, uint64_t seed, int preci
   if (!m || !out) return fail(QED_EINVAL, "null argument");
   *out = nullptr;
   if (chi < 1 || chi > 512) return fail(QED_EINVAL, "chi out of range (1..512)");
-  if (precision != QED_PREC_FP64 && precision != QED_PREC_TF32 && precision != QED_PREC_BF16)
+  if (precision != QED_PREC_FP64 && precision != QED_PREC_TF32 && precision != QED_PREC_BF16 &&
+      precision != QED_PREC_TF32X3)
     return fail(QED_EINVAL, "unknown precision");
   int dev_count = 0;
   if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0)
@@ -223,12 +226,56 @@ QED_API int ttn_sweep(ttn_state* s, int32_t n_sweeps, double tol, int32_t max_kr
     if (out) {
       out->energy = st.energy;
       out->matvecs = st.matvecs;
+      out->matvecs_mixed = st.matvecs_mixed;
       out->node_updates = st.node_updates;
       out->not_converged = st.not_converged;
       out->max_rel_residual = st.max_residual;
       out->seconds = std::chrono::duration<double>(t1 - t0).count();
     }
     if (st.not_converged) return fail(QED_ENOCONV, "some node updates stopped above tolerance");
+    return QED_OK;)
+}
+
+QED_API int ttn_set_mixed_tol(ttn_state* s, double mixed_tol) {
+  if (!s) return fail(QED_EINVAL, "null state");
+  if (!(mixed_tol > 0.0) || !(mixed_tol < 1.0)) return fail(QED_EINVAL, "mixed_tol must lie in (0, 1)");
+  s->engine->mixed_tol = mixed_tol;
+  return QED_OK;
+}
+
+QED_API int ttn_last_update(ttn_state* s, int32_t* iters_fp64, int32_t* iters_mixed, double* rel_residual) {
+  if (!s) return fail(QED_EINVAL, "null state");
+  if (iters_fp64) *iters_fp64 = s->engine->last_lanczos_iters;
+  if (iters_mixed) *iters_mixed = s->engine->last_mixed_iters;
+  if (rel_residual) *rel_residual = s->engine->last_residual;
+  return QED_OK;
+}
+
+QED_API int ttn_set_profiling(ttn_state* s, int on) {
+  if (!s) return fail(QED_EINVAL, "null state");
+  s->engine->set_profiling(on != 0);
+  return QED_OK;
+}
+
+QED_API int ttn_reset_timing(ttn_state* s) {
+  if (!s) return fail(QED_EINVAL, "null state");
+  QED_TRY(s->engine->reset_timing(); return QED_OK;)
+}
+
+QED_API int ttn_kernel_timing(ttn_state* s, int kernel_class, double* ms, int64_t* launches, double* flops_alg,
+                              double* flops_exec, double* bytes_alg) {
+  if (!s) return fail(QED_EINVAL, "null state");
+  if (kernel_class < 0 || kernel_class >= qed::KC_COUNT) return fail(QED_EINVAL, "unknown kernel class");
+  QED_TRY(
+    qed::KernelTiming t[qed::KC_COUNT];
+    int rc = s->engine->kernel_timing(t);
+    if (rc) return engine_status(s->engine, rc);
+    const qed::KernelTiming& k = t[kernel_class];
+    if (ms) *ms = k.ms;
+    if (launches) *launches = k.launches;
+    if (flops_alg) *flops_alg = k.flops_alg;
+    if (flops_exec) *flops_exec = k.flops_exec;
+    if (bytes_alg) *bytes_alg = k.bytes_alg;
     return QED_OK;)
 }
 
@@ -408,6 +455,22 @@ QED_API int ttn_node_import(ttn_state* s, int32_t node, const double* buf, int64
     return engine_status(s->engine, rc);)
 }
 
+QED_API int ttn_load_tensors(ttn_state* s, const double* const* bufs, const int64_t* sizes, int32_t n_nodes) {
+  if (!s || !bufs || !sizes) return fail(QED_EINVAL, "null argument");
+  if (n_nodes != s->engine->n_nodes()) return fail(QED_EINVAL, "n_nodes mismatch");
+  QED_TRY(
+    std::vector<long long> sz(sizes, sizes + n_nodes);
+    int rc = s->engine->load_tensors(bufs, sz.data(), n_nodes);
+    if (rc == -1) return fail(QED_EINVAL, "tensor size mismatch");
+    return engine_status(s->engine, rc);)
+}
+
+QED_API int qed_launch_count(int64_t* count) {
+  if (!count) return fail(QED_EINVAL, "null argument");
+  *count = qed::launch_count();
+  return QED_OK;
+}
+
 QED_API int ttn_apply_heff(ttn_state* s, const double* x, double* y, int64_t n) {
   if (!s || !x || !y) return fail(QED_EINVAL, "null argument");
   const int64_t need = s->engine->node_size(s->engine->center());
@@ -418,7 +481,7 @@ QED_API int ttn_apply_heff(ttn_state* s, const double* x, double* y, int64_t n) 
     if (cudaMalloc(&dy, n * sizeof(double)) != cudaSuccess) { cudaFree(dx); return fail(QED_ENOMEM, "device allocation"); }
     cudaStream_t st = s->engine->stream();
     cudaMemcpyAsync(dx, x, n * sizeof(double), cudaMemcpyHostToDevice, st);
-    int rc = s->engine->apply_heff(dx, dy, -1);
+    int rc = s->engine->apply_heff_native(dx, dy);
     if (!rc) cudaMemcpyAsync(y, dy, n * sizeof(double), cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);
     cudaFree(dx);
@@ -431,7 +494,7 @@ QED_API int ttn_apply_heff(ttn_state* s, const double* x, double* y, int64_t n) 
 QED_API int ttn_apply_heff_device(ttn_state* s, const double* x_device, double* y_device, int64_t n) {
   if (!s || !x_device || !y_device) return fail(QED_EINVAL, "null argument");
   if (n != s->engine->node_size(s->engine->center())) return fail(QED_EINVAL, "size must equal the centre tensor size");
-  QED_TRY(return engine_status(s->engine, s->engine->apply_heff(x_device, y_device, -1));)
+  QED_TRY(return engine_status(s->engine, s->engine->apply_heff_native(x_device, y_device));)
 }
 
 }  // extern "C"

@@ -215,6 +215,14 @@ void KPlan::release() {
   cap_chunks = cap_outs = cap_tiles = cap_red = 0;
 }
 
+void TcPlan::release() {
+  void* ptrs[6] = {d_tiles, d_outs, d_chunks, d_adds, d_xjobs, d_wjobs};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  d_tiles = nullptr; d_outs = nullptr; d_chunks = nullptr; d_adds = nullptr; d_xjobs = nullptr; d_wjobs = nullptr;
+  for (size_t& c : cap) c = 0;
+}
+
 static KChunk make_chunk() {
   KChunk c;
   std::memset(&c, 0, sizeof(c));
@@ -405,6 +413,9 @@ Engine::Engine(const Params& p, int chi, uint64_t seed, int precision, cudaStrea
   tmp_ = (double*)dalloc(nmax_ * sizeof(double));
   d_scal_ = (double*)dalloc(8192 * sizeof(double));
   d_partial_ = (double*)dalloc(304 * (kMaxKrylov + 2) * sizeof(double));
+  d_err_ = (int*)dalloc(sizeof(int));
+  cudaMemsetAsync(d_err_, 0, sizeof(int), stream_);
+  mixed_tol = precision == PREC_TF32X3 ? 1e-7 : (precision == PREC_TF32 ? 1e-5 : 1e-4);
   init_tensors();
 }
 
@@ -413,6 +424,12 @@ Engine::~Engine() {
   for (auto& kv : site_ops_) delete kv.second;
   for (int i = 0; i < 3; ++i) heff_stage_[i].release();
   work_.release();
+  tc_.release();
+  if (xstage_) cudaFree(xstage_);
+  if (xstage32_) cudaFree(xstage32_);
+  if (wbuf_) cudaFree(wbuf_);
+  for (auto& r : ev_pending_) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (cudaEvent_t e : ev_pool_) cudaEventDestroy(e);
   if (scratch_) cudaFree(scratch_);
   if (zpool_) cudaFree(zpool_);
   if (V_) cudaFree(V_);
@@ -476,6 +493,7 @@ RowMap Engine::build_rowmap_sector(int node, const SiteOp* A, const SiteOp* B, i
       }
   }
   rm.src_sector = src_sec;
+  for (int r = 0; r < rows; ++r) rm.nnz += map[r] >= 0;
   if (src_sec < 0) return rm;
   if (need_val) {
     for (int r = 0; r < rows; ++r)
@@ -1139,6 +1157,15 @@ int Engine::compute_down(int node) {
 
 // ------------------------------------------------------------------ centre moves
 int Engine::move_to(int target) {
+  if (target == center_) return 0;
+  cudaEvent_t e0 = nullptr;
+  if (profiling_) ev_begin(&e0);
+  int rc = move_path(target);
+  if (profiling_) ev_end(e0, KC_MOVE, 0, 0, 0);
+  return rc;
+}
+
+int Engine::move_path(int target) {
   // path from centre to target through the lowest common ancestor
   std::vector<int> pa, pb;
   for (int x = center_; x >= 0; x = nodes_[x].parent) pa.push_back(x);
@@ -1172,6 +1199,8 @@ int Engine::move_to(int target) {
     cudaFree(R);
     if (rc) return rc;
     center_ = t;
+    tc_node_ = -1;
+    plan_node_ = -1;
     if (leg_c == 2) rc = compute_up(c);
     else rc = compute_down(t);
     if (rc) return rc;
@@ -1386,24 +1415,272 @@ int Engine::build_heff_plan(int node, int cls) {
   return check(cudaGetLastError(), "plan") ? 0 : -3;
 }
 
+bool Engine::mixed_node(int node) const {
+  (void)node;
+  return precision_ != PREC_FP64;
+}
+
 int Engine::apply_heff(const double* x, double* y, int cls) {
+  const long long n = layout_[center_].size;
+  const bool bottom = nodes_[center_].child_kind[0] == 0;
+  if (use_mixed_ && cls < 0 && bottom) {
+    if (x != x_in_) launch_copy(x, x_in_, n, stream_);
+    int rc = apply_heff_mixed();
+    if (rc) return rc;
+    if (y != y_out_) launch_copy(y_out_, y, n, stream_);
+    return check(cudaGetLastError(), "apply_heff (mixed)") ? 0 : -3;
+  }
   int rc = build_heff_plan(center_, cls);
   if (rc) return rc;
-  const long long n = layout_[center_].size;
   if (x != x_in_) launch_copy(x, x_in_, n, stream_);
-  const bool bottom = nodes_[center_].child_kind[0] == 0;
+  cudaEvent_t e0 = nullptr;
+  if (profiling_) ev_begin(&e0);
   if (!bottom && heff_z_elems_ > 0) {
     // Z blocks that no source block maps to must read as zero
     cudaMemsetAsync(zpool_, 0, heff_z_elems_ * sizeof(double), stream_);
   }
+  double flops = 0.0;
+  const int fp32 = (use_mixed_ && cls < 0) ? 1 : 0;
   for (int i = 0; i < 3; ++i) {
     KPlan& pl = heff_stage_[i];
     if (pl.tiles.empty()) continue;
-    launch_kc_gemm(pl.d_tiles, (int)pl.tiles.size(), pl.d_outs, pl.d_chunks, scratch_, stream_);
+    launch_kc_gemm(pl.d_tiles, (int)pl.tiles.size(), pl.d_outs, pl.d_chunks, scratch_, stream_, fp32);
     launch_kc_reduce(pl.d_outs, (int)pl.outs.size(), pl.d_red, (int)pl.red.size(), scratch_, stream_);
+    if (profiling_)
+      for (const KOutput& o : pl.outs)
+        for (int c = o.chunk_begin; c < o.chunk_end; ++c)
+          if (!pl.chunks[c].add) flops += 2.0 * o.M * o.N * pl.chunks[c].K;
   }
+  if (profiling_) ev_end(e0, bottom ? KC_HEFF_SIMT_BOTTOM : KC_HEFF_SIMT_UPPER, flops, flops, 0.0);
   if (y != y_out_) launch_copy(y_out_, y, n, stream_);
   return check(cudaGetLastError(), "apply_heff") ? 0 : -3;
+}
+
+// ------------------------------------------------------------------ mixed precision
+// Tensor-core plan of a bottom node: environment-coupled terms (and the
+// environment block Hamiltonian) become GEMM chunks with their operator
+// blocks converted to BF16 / FP32 and scaled by the term coefficient; terms
+// acting on the two sites only, and the constant, are FP64 epilogue adds.
+int Engine::build_tc_plan(int node) {
+  if (tc_node_ == node) return 0;
+  std::vector<HTerm> hts;
+  build_heff_terms(node, -1, &hts);
+  const Layout& L = layout_[node];
+  const Sectors& P = L.leg[2];
+  const int ns = (int)P.q.size();
+  const int d2 = P.total();
+  const int elem = precision_ == PREC_BF16 ? 2 : 4;
+  const bool split = precision_ == PREC_TF32X3;
+  const int xmul = split ? 2 : 1;   // staged row width in units of kpad
+  const int kmul = split ? 2 : 1;   // staged B row width in units of kpad
+  tc_.clear();
+  std::vector<long long> soff(ns, 0);
+  std::vector<int> kpad(ns);
+  long long xs = 0;
+  for (int i = 0; i < ns; ++i) {
+    kpad[i] = (P.dim[i] + 15) / 16 * 16;
+    soff[i] = xs;
+    xs += (long long)L.sec_rows[i] * kpad[i];
+  }
+  // operand staging holds xmul * xs elements; an FP32 copy (xs) serves the epilogue
+  if (xs > xstage_elems_) {
+    if (xstage_) { untrack(xstage_); cudaFree(xstage_); }
+    if (xstage32_) { untrack(xstage32_); cudaFree(xstage32_); xstage32_ = nullptr; }
+    xstage_elems_ = xs + xs / 4;
+    if (!check(cudaMalloc(&xstage_, 2 * xstage_elems_ * elem), "x staging")) return -2;
+    track(xstage_, 2 * xstage_elems_ * elem);
+    if (!check(cudaMalloc(&xstage32_, xstage_elems_ * 4), "x staging")) return -2;
+    track(xstage32_, xstage_elems_ * 4);
+  }
+  float* x32 = xstage32_;
+  for (int i = 0; i < ns; ++i) {
+    if (L.sec_rows[i] == 0) continue;
+    ConvJob j;
+    j.src = x_in_ + L.sec_off[i];
+    j.ld_src = P.dim[i];
+    j.cs_src = 1;
+    j.dst = (char*)xstage_ + xmul * soff[i] * elem;
+    j.dst32 = xstage32_ + soff[i];
+    j.rows = L.sec_rows[i];
+    j.cols = P.dim[i];
+    j.kpad = kpad[i];
+    j.scale = 1.0;
+    tc_.xjobs.push_back(j);
+    tc_.x_max_elems = std::max(tc_.x_max_elems, (long long)j.rows * j.kpad);
+  }
+  // W slots
+  long long wtot = 0;
+  struct WJ { int oc, ic; const double* op; double coef; long long off; };
+  std::vector<WJ> wj;
+  const double cst = constant_;
+  for (int oc = 0; oc < ns; ++oc) {
+    const int rows = L.sec_rows[oc];
+    if (rows == 0) continue;
+    TcOutput o;
+    o.y = y_out_ + L.sec_off[oc];
+    o.rows = rows;
+    o.n = P.dim[oc];
+    o.npad = kpad[oc];
+    o.chunk_begin = (int)tc_.chunks.size();
+    o.add_begin = (int)tc_.adds.size();
+    tc_.max_npad = std::max(tc_.max_npad, o.npad);
+    if (cst != 0.0) {
+      TcAdd a;
+      a.X32 = x32 + soff[oc];
+      a.map = nullptr;
+      a.val = nullptr;
+      a.alpha = cst;
+      a.ld = kpad[oc];
+      tc_.adds.push_back(a);
+    }
+    for (const HTerm& h : hts) {
+      const bool phys = h.op[0].kind == 2 || h.op[1].kind == 2;
+      const RowMap* rm = nullptr;
+      if (phys) {
+        if (h.op[0].kind == 2 && h.op[0].term < 0) rm = &site_ham_map(node, 0, h.op[0].cls)[oc];
+        else if (h.op[1].kind == 2 && h.op[1].term < 0) rm = &site_ham_map(node, 1, h.op[1].cls)[oc];
+        else rm = &rowmap(node, h.op[0].kind == 2 ? h.op[0].term : h.op[1].term)[oc];
+        if (rm->src_sector < 0) continue;
+      }
+      const int ic = phys ? rm->src_sector : oc;
+      if (h.op[2].kind == 1) {
+        if (P.find(P.q[ic] + h.op[2].shift) != oc) continue;
+        if (rm && rm->val) return -7;   // GEMM terms carry +-1 maps only
+        TcChunk c;
+        c.X = (char*)xstage_ + xmul * soff[ic] * elem;
+        c.map = rm ? rm->map : nullptr;
+        c.kpad = kmul * kpad[ic];
+        c.xstride = xmul * kpad[ic];
+        const long long welems = (long long)o.npad * c.kpad;
+        wj.push_back({oc, ic, h.op[2].ptr, h.coef, wtot});
+        c.W = (const void*)(intptr_t)wtot;   // patched below once the buffer exists
+        wtot += welems;
+        tc_.chunks.push_back(c);
+        tc_.max_kpad = std::max(tc_.max_kpad, c.kpad);
+        const double nnz = rm ? (double)rm->nnz : (double)rows;
+        tc_.flops_alg += 2.0 * nnz * P.dim[oc] * P.dim[ic];
+        tc_.flops_exec += 2.0 * ((rows + 127) / 128 * 128) * o.npad * kpad[ic] * (split ? 3 : 1);
+      } else {
+        if (ic != oc) continue;
+        TcAdd a;
+        a.X32 = x32 + soff[ic];
+        a.map = rm ? rm->map : nullptr;
+        a.val = rm ? rm->val : nullptr;
+        a.alpha = h.coef;
+        a.ld = kpad[ic];
+        tc_.adds.push_back(a);
+      }
+    }
+    o.chunk_end = (int)tc_.chunks.size();
+    o.add_end = (int)tc_.adds.size();
+    tc_.outs.push_back(o);
+    for (int r0 = 0; r0 < rows; r0 += 128) tc_.tiles.push_back({(int)tc_.outs.size() - 1, r0});
+  }
+  if (wtot > wbuf_elems_) {
+    if (wbuf_) { untrack(wbuf_); cudaFree(wbuf_); }
+    wbuf_elems_ = wtot + wtot / 4 + 1024;
+    if (!check(cudaMalloc(&wbuf_, wbuf_elems_ * elem), "W staging")) return -2;
+    track(wbuf_, wbuf_elems_ * elem);
+  }
+  for (TcChunk& c : tc_.chunks) c.W = (char*)wbuf_ + (intptr_t)c.W * elem;
+  if (wtot > 0) cudaMemsetAsync(wbuf_, 0, wtot * elem, stream_);
+  for (const WJ& w : wj) {
+    ConvJob j;
+    j.src = w.op + P.offset(w.oc) * (long long)d2 + P.offset(w.ic);
+    j.ld_src = d2;
+    j.cs_src = 1;
+    j.dst = (char*)wbuf_ + w.off * elem;
+    j.dst32 = nullptr;
+    j.rows = P.dim[w.oc];
+    j.cols = P.dim[w.ic];
+    j.kpad = kpad[w.ic];
+    j.scale = w.coef;
+    tc_.wjobs.push_back(j);
+    tc_.w_max_elems = std::max(tc_.w_max_elems, (long long)j.rows * j.kpad);
+  }
+  // algorithmic bytes: x staging read once, y written once (FP64), W read once
+  tc_.bytes_alg = (double)xs * xmul * elem + (double)L.size * 8.0 + (double)wtot * elem;
+  grow_upload(tc_.d_tiles, tc_.cap[0], tc_.tiles, stream_);
+  grow_upload(tc_.d_outs, tc_.cap[1], tc_.outs, stream_);
+  grow_upload(tc_.d_chunks, tc_.cap[2], tc_.chunks, stream_);
+  grow_upload(tc_.d_adds, tc_.cap[3], tc_.adds, stream_);
+  grow_upload(tc_.d_xjobs, tc_.cap[4], tc_.xjobs, stream_);
+  grow_upload(tc_.d_wjobs, tc_.cap[5], tc_.wjobs, stream_);
+  launch_convert(elem, split ? 2 : 0, tc_.d_wjobs, (int)tc_.wjobs.size(), tc_.w_max_elems, stream_);
+  tc_node_ = node;
+  return check(cudaGetLastError(), "tc plan") ? 0 : -3;
+}
+
+int Engine::apply_heff_mixed() {
+  int rc = build_tc_plan(center_);
+  if (rc) return rc;
+  const int elem = precision_ == PREC_BF16 ? 2 : 4;
+  const int split = precision_ == PREC_TF32X3 ? 1 : 0;
+  launch_convert(elem, split, tc_.d_xjobs, (int)tc_.xjobs.size(), tc_.x_max_elems, stream_);
+  cudaEvent_t e0 = nullptr;
+  if (profiling_) ev_begin(&e0);
+  rc = launch_tc_heff(elem, split, tc_.d_tiles, (int)tc_.tiles.size(), tc_.d_outs, tc_.d_chunks, tc_.d_adds, tc_.max_kpad,
+                      tc_.max_npad, d_err_, stream_);
+  if (rc) {
+    err_ = "tensor-core H_eff: tile shape outside the supported range";
+    return rc;
+  }
+  if (profiling_) ev_end(e0, KC_TC_HEFF, tc_.flops_alg, tc_.flops_exec, tc_.bytes_alg);
+  return 0;
+}
+
+// ------------------------------------------------------------------ profiling
+cudaEvent_t Engine::ev_get() {
+  if (!ev_pool_.empty()) {
+    cudaEvent_t e = ev_pool_.back();
+    ev_pool_.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void Engine::ev_begin(cudaEvent_t* e) {
+  *e = ev_get();
+  cudaEventRecord(*e, stream_);
+}
+
+void Engine::ev_end(cudaEvent_t a, int cls, double fa, double fe, double ba) {
+  cudaEvent_t b = ev_get();
+  cudaEventRecord(b, stream_);
+  ev_pending_.push_back({a, b, cls, fa, fe, ba});
+  if (ev_pending_.size() > 4096) {
+    KernelTiming dummy[KC_COUNT];
+    kernel_timing(dummy);
+  }
+}
+
+void Engine::set_profiling(bool on) { profiling_ = on; }
+
+void Engine::reset_timing() {
+  KernelTiming dummy[KC_COUNT];
+  kernel_timing(dummy);
+  for (auto& t : timing_) t = KernelTiming();
+}
+
+int Engine::kernel_timing(KernelTiming out[KC_COUNT]) {
+  if (!check(cudaStreamSynchronize(stream_), "timing")) return -3;
+  for (auto& r : ev_pending_) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    KernelTiming& t = timing_[r.cls];
+    t.ms += ms;
+    t.launches += 1;
+    t.flops_alg += r.fa;
+    t.flops_exec += r.fe;
+    t.bytes_alg += r.ba;
+    ev_pool_.push_back(r.a);
+    ev_pool_.push_back(r.b);
+  }
+  ev_pending_.clear();
+  for (int i = 0; i < KC_COUNT; ++i) out[i] = timing_[i];
+  return 0;
 }
 
 // ------------------------------------------------------------------ Lanczos
@@ -1412,7 +1689,18 @@ int Engine::apply_heff(const double* x, double* y, int cls) {
 // pair of the tridiagonal is found on the device.  Stops when the
 // residual estimate |beta_k s_k| <= tol |theta|, restarting from the Ritz
 // vector when the Krylov space is full.
-int Engine::lanczos(int node, double tol, int max_krylov, double* energy, double* resid, int* iters) {
+int Engine::lanczos(int node, double tol, int max_krylov, bool mixed, int max_restarts, double* energy, double* resid,
+                    int* iters) {
+  cudaEvent_t e0 = nullptr;
+  if (profiling_) ev_begin(&e0);
+  int rc = lanczos_run(node, tol, max_krylov, mixed, max_restarts, energy, resid, iters);
+  if (profiling_) ev_end(e0, KC_LANCZOS, 0, 0, 0);
+  return rc;
+}
+
+int Engine::lanczos_run(int node, double tol, int max_krylov, bool mixed, int max_restarts, double* energy,
+                        double* resid, int* iters) {
+  use_mixed_ = mixed;
   const long long n = layout_[node].size;
   int kmax = std::min(std::max(max_krylov, 2), kMaxKrylov);
   if (kmax > n) kmax = (int)n;
@@ -1432,8 +1720,8 @@ int Engine::lanczos(int node, double tol, int max_krylov, double* energy, double
   const long long ld = nmax_;
   launch_copy(T_[node], xvec, n, stream_);
   int total_iters = 0;
-  double theta = 0.0, res = 0.0;
-  const int max_restarts = 50;
+  double theta = 0.0, res = 0.0, prev_res = 1e300;
+  int stalls = 0;
   for (int restart = 0; restart < max_restarts; ++restart) {
     launch_dot(xvec, xvec, n, d_partial_, nrm2, stream_);
     launch_scale_inv_sqrt(xvec, V_, n, nrm2, stream_);
@@ -1469,7 +1757,15 @@ int Engine::lanczos(int node, double tol, int max_krylov, double* energy, double
     // Ritz vector x = V s
     launch_combine(V_, ld, k, svec, xvec, n, stream_);
     if (done) break;
+    // a low-precision operator stops improving at its rounding level: two
+    // restart cycles without a 2 % gain end the low-precision phase
+    if (mixed) {
+      stalls = res > 0.98 * prev_res ? stalls + 1 : 0;
+      if (stalls >= 2) break;
+    }
+    prev_res = std::min(prev_res, res);
   }
+  use_mixed_ = false;
   // normalise
   launch_dot(xvec, xvec, n, d_partial_, nrm2, stream_);
   launch_scale_inv_sqrt(xvec, T_[node], n, nrm2, stream_);
@@ -1479,16 +1775,35 @@ int Engine::lanczos(int node, double tol, int max_krylov, double* energy, double
   return check(cudaStreamSynchronize(stream_), "lanczos end") ? 0 : -3;
 }
 
+// Node update.  FP64 path: Lanczos to tol.  Mixed path (bottom nodes):
+// Lanczos with tensor-core matvecs to max(tol, mixed_tol), then the same
+// Lanczos restarted from that Ritz vector with FP64 matvecs until the FP64
+// residual meets tol (the FP64 residual correction).
 int Engine::optimize_node(int node, double tol, int max_krylov, SweepStats* st, double* e) {
   int rc = move_to(node);
   if (rc) return rc;
   double energy = 0, res = 0;
-  int iters = 0;
-  rc = lanczos(node, tol, max_krylov, &energy, &res, &iters);
+  int iters = 0, mixed_iters = 0;
+  if (mixed_node(node)) {
+    cudaMemsetAsync(d_err_, 0, sizeof(int), stream_);
+    rc = lanczos(node, std::max(tol, mixed_tol), max_krylov, true, 50, &energy, &res, &mixed_iters);
+    if (rc) return rc;
+    int herr = 0;
+    cudaMemcpyAsync(&herr, d_err_, sizeof(int), cudaMemcpyDeviceToHost, stream_);
+    if (!check(cudaStreamSynchronize(stream_), "mixed phase")) return -3;
+    if (herr) {
+      err_ = "tensor-core H_eff: an mbarrier wait hit its iteration limit";
+      return -6;
+    }
+  }
+  rc = lanczos(node, tol, max_krylov, false, 50, &energy, &res, &iters);
   if (rc) return rc;
   last_lanczos_iters = iters;
+  last_mixed_iters = mixed_iters;
+  last_residual = res / std::max(1e-300, std::fabs(energy));
   if (st) {
-    st->matvecs += iters;
+    st->matvecs += iters + mixed_iters;
+    st->matvecs_mixed += mixed_iters;
     st->node_updates += 1;
     st->energy = energy;
     st->max_residual = std::max(st->max_residual, res / std::max(1e-300, std::fabs(energy)));
@@ -1595,6 +1910,23 @@ int Engine::node_import(int node, const std::vector<double>& host) {
   cudaMemcpyAsync(T_[node], host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, stream_);
   plan_node_ = -1;
   return check(cudaStreamSynchronize(stream_), "import") ? 0 : -3;
+}
+
+int Engine::load_tensors(const double* const* host, const long long* sizes, int n) {
+  if (n != (int)nodes_.size()) return -1;
+  for (int i = 0; i < n; ++i)
+    if (sizes[i] != layout_[i].size || !host[i]) return -1;
+  for (int i = 0; i < n; ++i)
+    cudaMemcpyAsync(T_[i], host[i], sizes[i] * sizeof(double), cudaMemcpyHostToDevice, stream_);
+  plan_node_ = -1;
+  tc_node_ = -1;
+  for (const TreeNode& nd : nodes_)
+    if (nd.parent >= 0) {
+      int rc = compute_up(nd.index);
+      if (rc) return rc;
+    }
+  center_ = (int)nodes_.size() - 1;
+  return check(cudaGetLastError(), "load") ? 0 : -3;
 }
 
 long long Engine::matvec_flops_algorithmic(int node) {

@@ -15,7 +15,7 @@
 
 namespace qed {
 
-enum Precision { PREC_FP64 = 0, PREC_TF32 = 1, PREC_BF16 = 2 };
+enum Precision { PREC_FP64 = 0, PREC_TF32 = 1, PREC_BF16 = 2, PREC_TF32X3 = 3 };
 
 // Block layout of a three-leg tensor T[a, b, c] whose blocks (q_a, q_b)
 // satisfy q_c = q_a + q_b - shift.  Blocks are ordered by (c-sector, q_a);
@@ -104,11 +104,52 @@ struct RowMap {
   int* map = nullptr;     // per output row, sign-encoded source row
   double* val = nullptr;  // optional per-row factor
   int src_sector = -1;    // source c-sector index (-1: all rows zero)
+  long long nnz = 0;      // rows with a nonzero entry
+};
+
+// Mixed-precision H_eff plan of a bottom node (tensor-core kernel).
+struct TcPlan {
+  std::vector<TcTile> tiles;
+  std::vector<TcOutput> outs;
+  std::vector<TcChunk> chunks;
+  std::vector<TcAdd> adds;
+  std::vector<ConvJob> xjobs, wjobs;
+  TcTile* d_tiles = nullptr;
+  TcOutput* d_outs = nullptr;
+  TcChunk* d_chunks = nullptr;
+  TcAdd* d_adds = nullptr;
+  ConvJob* d_xjobs = nullptr;
+  ConvJob* d_wjobs = nullptr;
+  size_t cap[6] = {0, 0, 0, 0, 0, 0};
+  long long x_max_elems = 0, w_max_elems = 0;
+  int max_kpad = 16, max_npad = 16;
+  double flops_alg = 0, flops_exec = 0, bytes_alg = 0;
+  void clear() {
+    tiles.clear(); outs.clear(); chunks.clear(); adds.clear(); xjobs.clear(); wjobs.clear();
+    x_max_elems = w_max_elems = 0; max_kpad = max_npad = 16; flops_alg = flops_exec = bytes_alg = 0;
+  }
+  void release();
+};
+
+// Per kernel-class timing of launches on the engine stream (CUDA events).
+// SIMT classes run FP64, or FP32 inside the low-precision phase of a mixed state.
+// KC_MOVE and KC_LANCZOS time whole phases (centre moves with QR and
+// operator updates; Lanczos calls including their products).
+enum KernelClass {
+  KC_TC_HEFF = 0, KC_HEFF_SIMT_BOTTOM = 1, KC_HEFF_SIMT_UPPER = 2, KC_MOVE = 3, KC_LANCZOS = 4, KC_COUNT = 5
+};
+struct KernelTiming {
+  double ms = 0.0;
+  long long launches = 0;
+  double flops_alg = 0.0;
+  double flops_exec = 0.0;
+  double bytes_alg = 0.0;
 };
 
 struct SweepStats {
   double energy = 0.0;
   int matvecs = 0;
+  int matvecs_mixed = 0;
   int node_updates = 0;
   double max_residual = 0.0;
   int not_converged = 0;
@@ -127,10 +168,20 @@ class Engine {
   int site_probabilities(std::vector<double>* probs);
   int node_export(int node, std::vector<double>* host);
   int node_import(int node, const std::vector<double>& host);
+  // Replace every tensor (tree isometric towards the root, root normalised)
+  // and rebuild all renormalized operators; the centre becomes the root.
+  int load_tensors(const double* const* host, const long long* sizes, int n);
   int move_to(int target);
   int optimize_node(int node, double tol, int max_krylov, SweepStats* st, double* e);
   // H_eff x at the current centre (x, y device pointers, centre layout).
   int apply_heff(const double* x, double* y, int cls_filter);
+  // H_eff x in the state's precision (tensor cores at bottom nodes when mixed)
+  int apply_heff_native(const double* x, double* y) {
+    use_mixed_ = precision_ != PREC_FP64;
+    int rc = apply_heff(x, y, -1);
+    use_mixed_ = false;
+    return rc;
+  }
   long long node_size(int node) const { return layout_[node].size; }
   int center() const { return center_; }
   int n_nodes() const { return (int)nodes_.size(); }
@@ -144,6 +195,15 @@ class Engine {
   long long matvec_flops_algorithmic(int node);
   long long device_bytes() const { return bytes_; }
   int last_lanczos_iters = 0;
+  int last_mixed_iters = 0;
+  double last_residual = 0.0;
+  // kernel timing (enabled by set_profiling): resolved on read
+  void set_profiling(bool on);
+  int kernel_timing(KernelTiming out[KC_COUNT]);
+  void reset_timing();
+  int precision() const { return precision_; }
+  // mixed path tuning: residual target of the low-precision phase
+  double mixed_tol = 0.0;
 
  private:
   Params p_;
@@ -180,6 +240,26 @@ class Engine {
   double* scratch_ = nullptr;
   long long scratch_elems_ = 0;
   KPlan work_;
+  // mixed-precision state
+  TcPlan tc_;
+  int tc_node_ = -1;
+  void* xstage_ = nullptr;      // BF16 or FP32 padded staging of x
+  float* xstage32_ = nullptr;   // FP32 padded staging (BF16 path)
+  long long xstage_elems_ = 0;
+  void* wbuf_ = nullptr;
+  long long wbuf_elems_ = 0;
+  int* d_err_ = nullptr;
+  bool profiling_ = false;
+  struct EvRec { cudaEvent_t a, b; int cls; double fa, fe, ba; };
+  std::vector<EvRec> ev_pending_;
+  std::vector<cudaEvent_t> ev_pool_;
+  KernelTiming timing_[KC_COUNT];
+  cudaEvent_t ev_get();
+  void ev_begin(cudaEvent_t* e);
+  void ev_end(cudaEvent_t a, int cls, double fa, double fe, double ba);
+  int build_tc_plan(int node);
+  int apply_heff_mixed();
+  bool mixed_node(int node) const;
   // Lanczos workspace
   double* V_ = nullptr;
   int kmax_alloc_ = 0;
@@ -223,7 +303,12 @@ class Engine {
   void ensure_scratch(long long elems);
   void ensure_zpool(long long elems);
   Layout shifted(int node, int shift) const;
-  int lanczos(int node, double tol, int max_krylov, double* energy, double* resid, int* iters);
+  int lanczos(int node, double tol, int max_krylov, bool mixed, int max_restarts, double* energy, double* resid,
+              int* iters);
+  int lanczos_run(int node, double tol, int max_krylov, bool mixed, int max_restarts, double* energy, double* resid,
+                  int* iters);
+  int move_path(int target);
+  bool use_mixed_ = false;   // current matvec precision inside lanczos
 };
 
 }  // namespace qed

@@ -5,6 +5,10 @@
 
 namespace qed {
 
+// Number of kernels launched by this library since load (all streams).
+long long launch_count();
+void count_launches(int n);
+
 // One contribution A(MxK) * B(KxN) to an output.  Element addressing:
 //   A[m,k] = sA * aval[m] * A[row*a_m + k*a_k],  amap[m] = (row << 1) | negate, -1 = zero row
 //   B[k,n] = sB * bval[k] * B[row*b_k + n*b_n],  bmap[k] likewise (maps and vals optional)
@@ -46,8 +50,10 @@ struct KTile {
 constexpr int KT_BM = 32;
 constexpr int KT_BN = 32;
 
+// fp32 != 0: same contraction with FP32 multiply-accumulate (operands
+// rounded to FP32 on load, results stored as FP64).
 void launch_kc_gemm(const KTile* tiles, int n_tiles, const KOutput* outs, const KChunk* chunks,
-                    double* scratch, cudaStream_t s);
+                    double* scratch, cudaStream_t s, int fp32 = 0);
 void launch_kc_reduce(const KOutput* outs, int n_outs, const int* red_list, int n_red, double* scratch,
                       cudaStream_t s);
 
@@ -94,5 +100,61 @@ void launch_cgs2_qr(double* X, const long long* xoff, const int* rows, const int
 // eigenvector with s[0] >= 0.  beta[k-1] is the trailing coupling.
 void launch_tridiag_lowest(const double* alpha, const double* beta, int k, double* out, double* svec,
                            cudaStream_t s);
+
+}  // namespace qed
+
+namespace qed {
+
+// ---- mixed-precision bottom-node H_eff (tcgen05) ----
+// One output c-sector of y (rows x n, FP64, row-major with ld = n) is the
+// sum of GEMM chunks  sign(r) * X[map(r), :] . W^T  accumulated in TMEM
+// (A rows gathered into shared memory, B = W, both K-major) and of add terms
+// alpha * sign(r) * val(r) * X32[map(r), :n] applied in FP32 in the epilogue.
+struct TcChunk {
+  const void* X;      // staging source sector matrix (BF16 or FP32), row stride xstride
+  const int* map;     // sign-encoded row map (nullable: identity)
+  const void* W;      // npad x kpad K-major B operand (alpha folded in)
+  int kpad;           // K of the staged rows, multiple of 16 (split: [hi | lo], 2 x part)
+  int xstride;        // elements per staged source row
+};
+struct TcAdd {
+  const float* X32;   // FP32 staging source sector matrix, row stride ld
+  const int* map;     // nullable: identity
+  const double* val;  // nullable
+  double alpha;
+  int ld;
+};
+struct TcOutput {
+  double* y;
+  int rows, n, npad;
+  int chunk_begin, chunk_end;
+  int add_begin, add_end;
+};
+struct TcTile {
+  int out;
+  int row0;
+};
+// One conversion job: dst (rows x kpad, zero padded) <- scale * src (rows x cols, ld_src), FP64 source.
+struct ConvJob {
+  const double* src;
+  long long ld_src;   // row stride of the source
+  long long cs_src;   // column stride of the source
+  void* dst;          // BF16 or FP32
+  float* dst32;       // optional second FP32 copy (same padded layout)
+  int rows, cols, kpad;
+  double scale;
+};
+
+// elem: 2 = BF16 operands (kind::f16), 4 = TF32 operands (kind::tf32).
+// split (TF32 only): A rows staged as [x_hi | x_lo] and B rows as [W_hi |
+// W_lo]; three sub-products x_hi W_hi + x_hi W_lo + x_lo W_hi whose sum
+// carries about 21 bits (x_lo W_lo dropped).
+// err: device flag set to 1 if a wait timed out (results then invalid).
+int launch_tc_heff(int elem, int split, const TcTile* tiles, int n_tiles, const TcOutput* outs,
+                   const TcChunk* chunks, const TcAdd* adds, int max_kpad, int max_npad, int* err, cudaStream_t s);
+// mode 0: plain (BF16 or FP32 by elem); mode 1: split x rows [hi | lo] of
+// width 2 kpad; mode 2: split W rows [hi | lo] of width 2 kpad.  hi is
+// the value with its 13 low mantissa bits cleared (what the TF32 units read).
+void launch_convert(int elem, int mode, const ConvJob* jobs, int n_jobs, long long max_elems, cudaStream_t s);
 
 }  // namespace qed

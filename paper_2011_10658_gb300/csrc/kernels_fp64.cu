@@ -3,11 +3,16 @@
 // GB300's FP64 rate is a small fraction of its tensor throughput, so these
 // kernels are simple register-tiled DFMA loops; the mixed-precision path
 // replaces the hot contraction with tensor-core kernels.
+#include <atomic>
 #include <cstdio>
 
 #include "kernels.cuh"
 
 namespace qed {
+
+static std::atomic<long long> g_launches{0};
+long long launch_count() { return g_launches.load(); }
+void count_launches(int n) { g_launches += n; }
 
 namespace {
 
@@ -41,18 +46,19 @@ __device__ __forceinline__ double load_b(const KChunk& c, int k, int n) {
   return scale * c.B[row * c.b_k + (long long)n * c.b_n];
 }
 
+template <typename T>
 __global__ void __launch_bounds__(THREADS) kc_gemm_kernel(const KTile* __restrict__ tiles,
                                                            const KOutput* __restrict__ outs,
                                                            const KChunk* __restrict__ chunks,
                                                            double* __restrict__ scratch) {
-  __shared__ double As[BK][KT_BM + 1];
-  __shared__ double Bs[BK][KT_BN + 1];
+  __shared__ T As[BK][KT_BM + 1];
+  __shared__ T Bs[BK][KT_BN + 1];
   const KTile tile = tiles[blockIdx.x];
   const KOutput out = outs[tile.out];
   const int tid = threadIdx.x;
   // each thread owns a 2x2 micro tile: rows ty*2.., cols tx*2..
   const int tx = tid % 16, ty = tid / 16;
-  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  T acc[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
   for (int ci = tile.chunk_begin; ci < tile.chunk_end; ++ci) {
     const KChunk c = chunks[ci];
     if (c.add) {
@@ -60,7 +66,7 @@ __global__ void __launch_bounds__(THREADS) kc_gemm_kernel(const KTile* __restric
       for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j) {
           int m = tile.m0 + ty * 2 + i, n = tile.n0 + tx * 2 + j;
-          if (m < out.M && n < out.N) acc[i][j] += c.alpha * load_a(c, m, n);
+          if (m < out.M && n < out.N) acc[i][j] += (T)(c.alpha * load_a(c, m, n));
         }
       continue;
     }
@@ -69,18 +75,18 @@ __global__ void __launch_bounds__(THREADS) kc_gemm_kernel(const KTile* __restric
       for (int e = tid; e < KT_BM * BK; e += THREADS) {
         int mm = e / BK, kk = e % BK;
         int m = tile.m0 + mm, k = k0 + kk;
-        As[kk][mm] = (m < out.M && k < c.K) ? c.alpha * load_a(c, m, k) : 0.0;
+        As[kk][mm] = (m < out.M && k < c.K) ? (T)(c.alpha * load_a(c, m, k)) : T(0);
       }
       for (int e = tid; e < KT_BN * BK; e += THREADS) {
         int kk = e / KT_BN, nn = e % KT_BN;
         int n = tile.n0 + nn, k = k0 + kk;
-        Bs[kk][nn] = (n < out.N && k < c.K) ? load_b(c, k, n) : 0.0;
+        Bs[kk][nn] = (n < out.N && k < c.K) ? (T)load_b(c, k, n) : T(0);
       }
       __syncthreads();
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
-        double a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
-        double b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
+        T a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
+        T b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
         acc[0][0] = fma(a0, b0, acc[0][0]);
         acc[0][1] = fma(a0, b1, acc[0][1]);
         acc[1][0] = fma(a1, b0, acc[1][0]);
@@ -94,10 +100,10 @@ __global__ void __launch_bounds__(THREADS) kc_gemm_kernel(const KTile* __restric
       int m = tile.m0 + ty * 2 + i, n = tile.n0 + tx * 2 + j;
       if (m >= out.M || n >= out.N) continue;
       if (tile.part >= 0) {
-        scratch[out.part_off + (long long)tile.part * out.M * out.N + (long long)m * out.N + n] = acc[i][j];
+        scratch[out.part_off + (long long)tile.part * out.M * out.N + (long long)m * out.N + n] = (double)acc[i][j];
       } else {
         double* p = out.C + (long long)m * out.c_m + (long long)n * out.c_n;
-        *p = out.accumulate ? (*p + acc[i][j]) : acc[i][j];
+        *p = out.accumulate ? (*p + (double)acc[i][j]) : (double)acc[i][j];
       }
     }
 }
@@ -478,9 +484,13 @@ int grid_for(long long n) {
 }  // namespace
 
 void launch_kc_gemm(const KTile* tiles, int n_tiles, const KOutput* outs, const KChunk* chunks, double* scratch,
-                    cudaStream_t s) {
+                    cudaStream_t s, int fp32) {
   if (n_tiles <= 0) return;
-  kc_gemm_kernel<<<n_tiles, THREADS, 0, s>>>(tiles, outs, chunks, scratch);
+  if (fp32)
+    kc_gemm_kernel<float><<<n_tiles, THREADS, 0, s>>>(tiles, outs, chunks, scratch);
+  else
+    kc_gemm_kernel<double><<<n_tiles, THREADS, 0, s>>>(tiles, outs, chunks, scratch);
+  count_launches(1);
 }
 
 void launch_kc_reduce(const KOutput* outs, int n_outs, const int* red_list, int n_red, double* scratch,
@@ -488,11 +498,14 @@ void launch_kc_reduce(const KOutput* outs, int n_outs, const int* red_list, int 
   if (n_red <= 0) return;
   dim3 grid(8, n_red);
   kc_reduce_kernel<<<grid, 256, 0, s>>>(outs, red_list, scratch);
+  count_launches(1);
 }
 
 void launch_dot(const double* x, const double* y, long long n, double* partial, double* out, cudaStream_t s) {
   dot_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(x, y, n, partial);
+  count_launches(1);
   finish_kernel<<<1, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, RED_BLOCKS, out);
+  count_launches(1);
 }
 
 void launch_multidot(const double* Q, long long ldq, int k, const double* w, long long n, double* partial,
@@ -500,55 +513,70 @@ void launch_multidot(const double* Q, long long ldq, int k, const double* w, lon
   if (k <= 0) return;
   dim3 grid(RED_BLOCKS, k);
   multidot_partial_kernel<<<grid, RED_THREADS, 0, s>>>(Q, ldq, k, w, n, partial);
+  count_launches(1);
   finish_kernel<<<k, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, RED_BLOCKS, out);
+  count_launches(1);
 }
 
 void launch_multiaxpy(const double* Q, long long ldq, int k, const double* c, double* w, long long n,
                       cudaStream_t s) {
   if (k <= 0) return;
   multiaxpy_kernel<<<grid_for(n), 256, 0, s>>>(Q, ldq, k, c, w, n);
+  count_launches(1);
 }
 
 void launch_combine(const double* Q, long long ldq, int k, const double* c, double* x, long long n,
                     cudaStream_t s) {
   combine_kernel<<<grid_for(n), 256, 0, s>>>(Q, ldq, k, c, x, n);
+  count_launches(1);
 }
 
-void launch_sqrt(const double* in, double* out, cudaStream_t s) { sqrt_kernel<<<1, 32, 0, s>>>(in, out); }
+void launch_sqrt(const double* in, double* out, cudaStream_t s) {
+  sqrt_kernel<<<1, 32, 0, s>>>(in, out);
+  count_launches(1);
+}
 
 void launch_axpby(const double* x, double* y, long long n, const double* a_dev, double a_const, double a_sign,
                   const double* b_dev, double b_const, cudaStream_t s) {
   axpby_kernel<<<grid_for(n), 256, 0, s>>>(x, y, n, a_dev, a_const, a_sign, b_dev, b_const);
+  count_launches(1);
 }
 
 void launch_scale_inv_sqrt(const double* x, double* y, long long n, const double* nrm2, cudaStream_t s) {
   scale_inv_sqrt_kernel<<<grid_for(n), 256, 0, s>>>(x, y, n, nrm2);
+  count_launches(1);
 }
 
 void launch_copy(const double* x, double* y, long long n, cudaStream_t s) {
   copy_kernel<<<grid_for(n), 256, 0, s>>>(x, y, n);
+  count_launches(1);
 }
 
 void launch_fill_uniform(double* x, long long n, uint64_t seed, uint64_t start, cudaStream_t s) {
   if (n <= 0) return;
   fill_uniform_kernel<<<grid_for(n), 256, 0, s>>>(x, n, seed, start);
+  count_launches(1);
 }
 
 void launch_add_scaled(const double* x, double* y, long long n, double a, cudaStream_t s) {
   add_scaled_kernel<<<grid_for(n), 256, 0, s>>>(x, y, n, a);
+  count_launches(1);
 }
 
 void launch_zero(double* x, long long n, cudaStream_t s) {
   if (n <= 0) return;
   zero_kernel<<<grid_for(n), 256, 0, s>>>(x, n);
+  count_launches(1);
 }
 
 void launch_to_float(const double* x, float* y, long long n, cudaStream_t s) {
   to_float_kernel<<<grid_for(n), 256, 0, s>>>(x, y, n);
+  count_launches(1);
 }
 
 void launch_to_double(const float* x, double* y, long long n, cudaStream_t s) {
   to_double_kernel<<<grid_for(n), 256, 0, s>>>(x, y, n);
+  count_launches(1);
 }
 
 void launch_cholesky_inv(double* G, double* Rinv, const long long* off, const int* n, const int* ld, int count,
@@ -561,17 +589,20 @@ void launch_cholesky_inv(double* G, double* Rinv, const long long* off, const in
   }
   cholesky_inv_kernel<<<count, 256, (size_t)max_n * max_n * sizeof(double), s>>>(G, Rinv, off, n, ld, status,
                                                                                   ill_cond);
+  count_launches(1);
 }
 
 void launch_cgs2_qr(double* X, const long long* xoff, const int* rows, const int* cols, int count, double* R,
                     const long long* roff, int ldr, double dep_tol, double accept, cudaStream_t s) {
   if (count <= 0) return;
   cgs2_qr_kernel<<<count, QR_THREADS, 0, s>>>(X, xoff, rows, cols, R, roff, ldr, dep_tol, accept);
+  count_launches(1);
 }
 
 void launch_tridiag_lowest(const double* alpha, const double* beta, int k, double* out, double* s,
                            cudaStream_t st) {
   tridiag_lowest_kernel<<<1, 32, 0, st>>>(alpha, beta, k, out, s);
+  count_launches(1);
 }
 
 }  // namespace qed

@@ -128,6 +128,10 @@ void build_site_op(int parity, const OpKey& key, SiteOp* out) {
       if (row[1 + key.a] == key.b) { out->src[in] = (int16_t)in; out->val[in] = 1.0; }
       continue;
     }
+    if (key.kind == OP_PC) {
+      if (row[1 + key.a] != key.b) { out->src[in] = (int16_t)in; out->val[in] = 1.0; }
+      continue;
+    }
     if (key.kind == OP_N) {
       if (row[0] == 1) { out->src[in] = (int16_t)in; out->val[in] = 1.0; }
       continue;
@@ -269,9 +273,11 @@ void build_terms(const Params& p, std::vector<Term>* terms, double* constant) {
     for (int mu = 0; mu < 3; ++mu) {
       int y = lat.neighbour(x, mu, +1);
       if (y < 0) continue;
-      for (int k = 0; k < 3; ++k) push(-p.nu, CLS_NU, {{x, key(OP_P, 3 + mu, k)}, {y, key(OP_P, mu, 2 - k)}});
+      // nu (1 - delta_{2,L}) = nu sum_k P^k_x (1 - P^{2-k}_y): non-negative terms, no constant
+      for (int k = 0; k < 3; ++k) push(p.nu, CLS_NU, {{x, key(OP_P, 3 + mu, k)}, {y, key(OP_PC, mu, 2 - k)}});
     }
-  *constant = p.nu * n_links;
+  (void)n_links;
+  *constant = 0.0;
 }
 
 // ---------------------------------------------------------------- tree

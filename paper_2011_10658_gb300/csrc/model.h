@@ -21,6 +21,7 @@ enum OpKind : int {
   OP_N = 5,      // psi^dag psi                (mass term)
   OP_E2 = 6,     // sum over a half-link mask of (1 - k_j)^2 (Eq. (10) squared)
   OP_DIAG = 7,   // arbitrary diagonal (site Hamiltonian)
+  OP_PC = 8,     // 1 - projector on k_j = k  (penalty complement)
 };
 
 struct OpKey {

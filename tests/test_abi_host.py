@@ -61,7 +61,8 @@ def _dense(src, val):
 
 KEYS = [(("M", j), ("M", j, 0)) for j in range(6)] + [(("Md", j), ("MD", j, 0)) for j in range(6)] + \
        [(("C", i, j), ("C", i, j)) for i in range(6) for j in range(6) if i != j] + \
-       [(("P", j, k), ("P", j, k)) for j in range(6) for k in range(3)] + [(("n",), ("N", 0, 0))]
+       [(("P", j, k), ("P", j, k)) for j in range(6) for k in range(3)] + \
+       [(("PC", j, k), ("PC", j, k)) for j in range(6) for k in range(3)] + [(("n",), ("N", 0, 0))]
 
 
 @pytest.mark.parametrize("parity", [1, -1])
@@ -86,7 +87,7 @@ def test_local_op_errors(q):
         q.local_op(1, "C", 2, 2)
 
 
-KIND = {"M": 1, "Md": 2, "C": 3, "P": 4, "n": 5, "E2": 6}
+KIND = {"M": 1, "Md": 2, "C": 3, "P": 4, "n": 5, "E2": 6, "PC": 8}
 CLS = {"t": 0, "m": 1, "ge2": 2, "cB": 3, "nu": 4}
 
 
@@ -101,7 +102,7 @@ def _oracle_terms(p):
                 ops.append((s, KIND[k], key[1], 0))
             elif k == "C":
                 ops.append((s, KIND[k], key[1], key[2]))
-            elif k == "P":
+            elif k in ("P", "PC"):
                 ops.append((s, KIND[k], key[1], key[2]))
             elif k == "n":
                 ops.append((s, KIND[k], 0, 0))

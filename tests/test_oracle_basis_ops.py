@@ -96,13 +96,14 @@ def test_odd_operator_leaves_gauge_span():
 
 KEYS = [("M", j) for j in range(6)] + [("Md", j) for j in range(6)] + \
        [("C", i, j) for i in range(6) for j in range(6) if i != j] + \
-       [("P", j, k) for j in range(6) for k in range(3)] + [("n",)]
+       [("P", j, k) for j in range(6) for k in range(3)] + [("PC", j, k) for j in range(6) for k in range(3)] + \
+       [("n",)]
 
 
 @pytest.mark.parametrize("parity", [1, -1])
 def test_local_ops_monomial_and_charge(parity):
     q = basis.charges(parity)
-    shift = {"M": 1, "Md": -1, "C": 0, "P": 0, "n": 0}
+    shift = {"M": 1, "Md": -1, "C": 0, "P": 0, "PC": 0, "n": 0}
     for key in KEYS:
         M = fock.site_op(key, parity).toarray()
         nz = M != 0

@@ -96,7 +96,7 @@ def test_lattice_and_tree_counts(L, counts):
     terms, const = model.build_terms(model.Params(*L))
     n_links, n_plaq = counts[1], counts[2]
     assert len(terms) == 2 * lat.n_sites + 5 * n_links + 2 * n_plaq
-    assert const == 10.0 * n_links
+    assert const == 0.0
 
 
 def test_tree_structure_4x4x4():
@@ -173,6 +173,26 @@ def test_allocation_rule_small():
     assert tree.allocate(6, w, cap, 1, 2, 0) == {-1: 2, 0: 3, 1: 1}
     # caps bind and the surplus moves on
     assert tree.allocate(6, w, {-1: 10, 0: 1, 1: 10}, 1, 2, 0) == {-1: 3, 0: 1, 1: 2}
+
+
+def test_penalty_rewrite_equals_eq16():
+    """nu sum_k P^k_x (1 - P^{2-k}_y) equals nu (1 - delta_{2, k_x + k_y}) on
+    every two-site state (Eq. (16))."""
+    from oracle import fock
+    p = model.Params(2, 1, 1, t=0.0, m=0.0, ge2=0.0, cB=0.0, nu=7.0, Q=0)
+    terms, const = model.build_terms(p)
+    assert const == 0.0
+    tabs = [np.asarray(fock.site_op(("P", 3, 0), s).diagonal()) for s in (1, -1)]
+    from oracle import basis
+    b0, b1 = basis.enumerate_basis(1), basis.enumerate_basis(-1)
+    H = np.zeros((267, 267))
+    for tm in terms:
+        (s0, k0), (s1, k1) = tm.ops
+        d0 = fock.site_op(k0, 1).diagonal()
+        d1 = fock.site_op(k1, -1).diagonal()
+        H += tm.coef * np.outer(d0, d1)
+    L = b0[:, 1 + 3][:, None] + b1[:, 1 + 0][None, :]
+    np.testing.assert_array_equal(H, 7.0 * (L != 2))
 
 
 def test_qr_positive():
