@@ -365,6 +365,27 @@ def run_native(args):
         dist.destroy_process_group()
 
 
+def run_heff_only(args):
+    """Profiling aid: the workload state with its centre at bottom node 0
+    and --steps H_eff x products on device buffers (no sweep)."""
+    import torch
+    import paper_2011_10658_gb300 as q
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    c = workloads.qed_couplings(G2)
+    s = q.TTN(q.Model(*L, Q=Q, **c), CHI, seed=SEED, precision=args.precision, stream=stream.cuda_stream)
+    s.move_center(args.node)
+    n = s.node_size(args.node)
+    x = torch.randn(n, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(args.warmup + args.steps):
+        s.apply_heff_device(x.data_ptr(), y.data_ptr(), n)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "heff", "node": args.node, "size": n, "products": args.warmup + args.steps,
+                      "norm": float(y.norm().item())}), flush=True)
+    s.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -376,11 +397,16 @@ def main():
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--mode", default="sweep", choices=["sweep", "heff"],
+                    help="heff: only H_eff x products at --node (profiling aid)")
+    ap.add_argument("--node", type=int, default=0)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "heff":
+        run_heff_only(args)
     else:
         run_native(args)
 
