@@ -252,6 +252,7 @@ def run_native(args):
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     ev0.record(stream)
     stats = []
     for _ in range(args.steps):
@@ -260,12 +261,13 @@ def run_native(args):
         energies.append(st["energy"])
     ev1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     barrier()
     elapsed_ms = ev0.elapsed_time(ev1)
     launches = q.launch_count() - launches0
     clocks = sampler.stop()
-    kt = {k: s.kernel_timing(k) for k in ("tc_heff", "heff_simt_bottom", "heff_simt_upper")}
-    flops = sum(v["flops_alg"] for v in kt.values())
+    kt = {k: s.kernel_timing(k) for k in ("tc_heff", "heff_simt_bottom", "heff_simt_upper", "move", "lanczos")}
+    flops = sum(kt[k]["flops_alg"] for k in ("tc_heff", "heff_simt_bottom", "heff_simt_upper"))
     if world > 1:
         t = torch.tensor([elapsed_ms, flops], device="cuda", dtype=torch.float64)
         mx = t.clone()
@@ -275,8 +277,8 @@ def run_native(args):
         elapsed_ms, flops = mx[0].item(), sm[1].item()
     value = flops / (elapsed_ms * 1e-3) / 1e12
 
-    # dominant kernel roofline
-    dom = max(kt, key=lambda k: kt[k]["ms"])
+    # dominant kernel roofline (kernel classes only, not whole phases)
+    dom = max(("tc_heff", "heff_simt_bottom", "heff_simt_upper"), key=lambda k: kt[k]["ms"])
     d = kt[dom]
     pk, src = peaks()
     per_launch_ms = d["ms"] / max(1, d["launches"])
@@ -321,6 +323,22 @@ def run_native(args):
     e2e = {"value": e2e_flops / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": h2d + 8, "seconds_per_step": e2e_s / args.steps}
 
+    # per-update |dE|/|E| on identical H_eff: the same node update from the
+    # same state, once with FP64 products and once in the state's precision
+    per_update = None
+    if args.precision != "fp64" and rank == 0:
+        rows = []
+        for node in (0, 1, 16, 31, 32, 48, 56, 62):
+            s.move_center(node)
+            t0 = s.node_export(node)
+            s.set_precision("fp64")
+            e64 = s.optimize_node(node, tol=TOL, max_krylov=KRYLOV)
+            s.node_import(node, t0)
+            s.set_precision(args.precision)
+            em = s.optimize_node(node, tol=TOL, max_krylov=KRYLOV)
+            rows.append({"node": node, "e_fp64": e64, "e_mixed": em, "rel_dE": abs(em - e64) / abs(e64)})
+        per_update = {"nodes": rows, "max_rel_dE": max(r["rel_dE"] for r in rows)}
+
     # FP64 GPU path on the same workload and sweeps for |dE|/|E|
     compare = None
     if args.compare_fp64 and args.precision != "fp64" and rank == 0:
@@ -357,7 +375,8 @@ def run_native(args):
             "energy": energies[-1],
             "matvecs_per_sweep": total_mv / args.steps, "mixed_matvecs_per_sweep": mixed_mv / args.steps,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": launches, "kernels": kt, "fp64_comparison": compare,
+            "gpu_launches": launches, "kernels": kt, "per_update_vs_fp64": per_update,
+            "fp64_trajectory_comparison": compare,
         }
         print(json.dumps(line), flush=True)
     s.close()

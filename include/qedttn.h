@@ -145,6 +145,9 @@ int ttn_sweep(ttn_state *s, int32_t n_sweeps, double tol, int32_t max_krylov, tt
  * vector with FP64 products until the FP64 residual reaches tol.  Default
  * mixed_tol: 1e-7 (TF32X3), 1e-5 (TF32), 1e-4 (BF16). */
 int ttn_set_mixed_tol(ttn_state *s, double mixed_tol);
+/* Switch the product precision of an existing state (QED_PREC_*); resets
+ * mixed_tol to its default for that precision. */
+int ttn_set_precision(ttn_state *s, int precision);
 /* Last node update: FP64 and mixed Lanczos iterations, |beta s| / |theta|. */
 int ttn_last_update(ttn_state *s, int32_t *iters_fp64, int32_t *iters_mixed, double *rel_residual);
 

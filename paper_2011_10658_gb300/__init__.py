@@ -134,6 +134,9 @@ class TTN:
         check(lib().ttn_optimize_node(self._h, node, tol, max_krylov, ctypes.byref(e)))
         return e.value
 
+    def set_precision(self, precision):
+        check(lib().ttn_set_precision(self._h, PREC[precision]))
+
     def set_mixed_tol(self, tol):
         check(lib().ttn_set_mixed_tol(self._h, tol))
 

@@ -236,6 +236,15 @@ QED_API int ttn_sweep(ttn_state* s, int32_t n_sweeps, double tol, int32_t max_kr
     return QED_OK;)
 }
 
+QED_API int ttn_set_precision(ttn_state* s, int precision) {
+  if (!s) return fail(QED_EINVAL, "null state");
+  if (precision != QED_PREC_FP64 && precision != QED_PREC_TF32 && precision != QED_PREC_BF16 &&
+      precision != QED_PREC_TF32X3)
+    return fail(QED_EINVAL, "unknown precision");
+  s->engine->set_precision(precision);
+  return QED_OK;
+}
+
 QED_API int ttn_set_mixed_tol(ttn_state* s, double mixed_tol) {
   if (!s) return fail(QED_EINVAL, "null state");
   if (!(mixed_tol > 0.0) || !(mixed_tol < 1.0)) return fail(QED_EINVAL, "mixed_tol must lie in (0, 1)");

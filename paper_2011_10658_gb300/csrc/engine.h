@@ -202,6 +202,11 @@ class Engine {
   int kernel_timing(KernelTiming out[KC_COUNT]);
   void reset_timing();
   int precision() const { return precision_; }
+  void set_precision(int p) {
+    precision_ = p;
+    tc_node_ = -1;
+    mixed_tol = p == PREC_TF32X3 ? 1e-7 : (p == PREC_TF32 ? 1e-5 : 1e-4);
+  }
   // mixed path tuning: residual target of the low-precision phase
   double mixed_tol = 0.0;
 
