@@ -216,6 +216,27 @@ int ttn_apply_heff(ttn_state *s, const double *x, double *y, int64_t n);
 /* Same with device buffers on the state's stream (no host copies). */
 int ttn_apply_heff_device(ttn_state *s, const double *x_device, double *y_device, int64_t n);
 
+/* y = H_eff x at the current centre, allocating nothing: no cudaMalloc,
+ * cudaFree or other allocating routine is called, on the device or the
+ * host.  The paper has no counterpart; this exists for callers whose
+ * device memory is owned by another allocator (a framework pool or an arena
+ * fixed at start-up) and who cannot let a library allocate or free device
+ * memory, which would also synchronise the device.
+ *
+ * Same product and FP64 grouped-GEMM kernel as ttn_apply_heff_device on an
+ * FP64 state; x_device and y_device (n doubles, centre layout) are used in
+ * place.  The kernel's work list lives in one file-scope device array of
+ * 4 MiB that every GPU loading the library holds until the process exits.
+ * The first call on a device looks up that array's device address once
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call rewrites the array, so calls that overlap on the GPU (from
+ * different streams or threads) race; calls on one stream are ordered.
+ * The centre must be a bottom node whose row maps and environment
+ * operators exist (any state whose centre was moved there by ttn_move_center
+ * or a sweep).  Errors: QED_EUNSUPPORTED for another centre or a work list
+ * larger than the array, QED_EINVAL for a size mismatch. */
+int ttn_apply_heff_device_noalloc(ttn_state *s, const double *x_device, double *y_device, int64_t n);
+
 const char *qed_last_error(void);
 
 #ifdef __cplusplus

@@ -225,3 +225,8 @@ class TTN:
 
     def apply_heff_device(self, x_ptr, y_ptr, n):
         check(lib().ttn_apply_heff_device(self._h, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), n))
+
+    def apply_heff_device_noalloc(self, x_ptr, y_ptr, n):
+        """Same product as apply_heff_device in FP64 at a bottom-node centre,
+        with no memory allocated by the call (see include/qedttn.h)."""
+        check(lib().ttn_apply_heff_device_noalloc(self._h, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), n))

@@ -65,6 +65,7 @@ SIGNATURES = [
     ("qed_launch_count", c_int, [c_int64_p]),
     ("ttn_apply_heff", c_int, [c_void_p, c_double_p, c_double_p, c_int64]),
     ("ttn_apply_heff_device", c_int, [c_void_p, c_void_p, c_void_p, c_int64]),
+    ("ttn_apply_heff_device_noalloc", c_int, [c_void_p, c_void_p, c_void_p, c_int64]),
 ]
 
 STATUS = {0: "QED_OK", -1: "QED_EINVAL", -2: "QED_ENOMEM", -3: "QED_ECUDA", -4: "QED_ENOCONV",

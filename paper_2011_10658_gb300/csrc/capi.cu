@@ -9,6 +9,7 @@
 #include "../../include/qedttn.h"
 #include "engine.h"
 #include "model.h"
+#include "state.h"
 
 namespace {
 thread_local std::string g_err;
@@ -32,17 +33,8 @@ int engine_status(qed::Engine* e, int rc) {
 bool pow2(int v) { return v >= 1 && (v & (v - 1)) == 0; }
 }  // namespace
 
-struct qed_model {
-  qed::Params p;
-  std::vector<qed::Term> terms;
-  double constant = 0.0;
-  std::vector<qed::TreeNode> nodes;
-};
+void qed_set_last_error(const char* msg) { g_err = msg; }
 
-struct ttn_state {
-  qed::Engine* engine = nullptr;
-  const qed_model* model = nullptr;
-};
 
 #define QED_TRY(...)                                    \
   try {                                                 \

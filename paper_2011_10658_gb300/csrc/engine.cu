@@ -1929,6 +1929,113 @@ int Engine::load_tensors(const double* const* host, const long long* sizes, int 
   return check(cudaGetLastError(), "load") ? 0 : -3;
 }
 
+int Engine::noalloc_worklist(const double* x, double* y, KTile* tiles, int max_tiles, KOutput* outs, int max_outs,
+                             KChunk* chunks, int max_chunks, int* n_tiles, int* n_outs, int* n_chunks) {
+  const int node = center_;
+  const TreeNode& nd = nodes_[node];
+  if (nd.child_kind[0] != 0 || nd.child_kind[1] != 0) {
+    err_ = "the centre is not a bottom node";
+    return -7;
+  }
+  const Layout& L = layout_[node];
+  const Sectors& P = L.leg[2];
+  const int d2 = P.total();
+  const bool root = nd.parent < 0;
+  const int sl = nd.child[0], sr = nd.child[1];
+  int no = 0, nc = 0, nt = 0;
+  auto find_maps = [&](int key) -> const std::vector<RowMap>* {
+    auto it = rowmaps_.find(std::make_pair(node, key));
+    return it == rowmaps_.end() ? nullptr : &it->second;
+  };
+  for (size_t oc = 0; oc < P.q.size(); ++oc) {
+    const int rows = L.sec_rows[oc];
+    if (rows == 0) continue;
+    const int dc = P.dim[oc];
+    if (no >= max_outs) { err_ = "work list: too many outputs"; return -2; }
+    KOutput& o = outs[no];
+    o.C = y + L.sec_off[oc];
+    o.c_m = dc;
+    o.c_n = 1;
+    o.M = rows;
+    o.N = dc;
+    o.chunk_begin = nc;
+    o.accumulate = 0;
+    o.n_parts = 1;
+    o.part_off = 0;
+    auto push = [&](const KChunk& c) -> bool {
+      if (nc >= max_chunks) return false;
+      chunks[nc++] = c;
+      return true;
+    };
+    if (constant_ != 0.0) {
+      KChunk c = make_chunk();
+      c.A = x + L.sec_off[oc]; c.a_m = dc; c.a_k = 1; c.add = 1; c.alpha = constant_;
+      if (!push(c)) { err_ = "work list: too many chunks"; return -2; }
+    }
+    // single-site terms of both sites: the all-class diagonal if present,
+    // otherwise one map per coupling class
+    for (int leg = 0; leg < 2; ++leg) {
+      const std::vector<RowMap>* all = find_maps(-1000 - 10 * leg);
+      for (int cls = all ? -1 : 0; cls < (all ? 0 : N_CLASSES); ++cls) {
+        const std::vector<RowMap>* maps = find_maps(-1000 - 10 * leg - (cls + 1));
+        if (!maps) { err_ = "site map missing at this centre"; return -7; }
+        const RowMap& rm = (*maps)[oc];
+        if (rm.src_sector < 0) continue;
+        KChunk c = make_chunk();
+        c.A = x + L.sec_off[rm.src_sector]; c.a_m = P.dim[rm.src_sector]; c.a_k = 1;
+        c.amap = rm.map; c.aval = rm.val; c.add = 1;
+        if (!push(c)) { err_ = "work list: too many chunks"; return -2; }
+      }
+    }
+    if (!root) {
+      KChunk c = make_chunk();
+      c.A = x + L.sec_off[oc]; c.a_m = dc; c.a_k = 1;
+      c.B = down_[node].Htot + P.offset((int)oc) * (long long)d2 + P.offset((int)oc); c.b_k = 1; c.b_n = d2;
+      c.K = dc;
+      if (!push(c)) { err_ = "work list: too many chunks"; return -2; }
+    }
+    for (int k = 0; k < (int)terms_.size(); ++k) {
+      bool t[3] = {false, false, false};
+      for (auto& so : terms_[k].ops) {
+        if (so.first == sl) t[0] = true;
+        else if (so.first == sr) t[1] = true;
+        else t[2] = true;
+      }
+      if ((int)t[0] + (int)t[1] + (int)t[2] < 2) continue;
+      const std::vector<RowMap>* maps = find_maps(k);
+      if (!maps) { err_ = "row map missing at this centre"; return -7; }
+      const RowMap& rm = (*maps)[oc];
+      if (rm.src_sector < 0) continue;
+      const int ic = rm.src_sector;
+      KChunk c = make_chunk();
+      c.A = x + L.sec_off[ic]; c.a_m = P.dim[ic]; c.a_k = 1;
+      c.amap = rm.map; c.aval = rm.val; c.alpha = terms_[k].coef;
+      if (t[2]) {
+        auto it = down_[node].term.find(k);
+        if (it == down_[node].term.end()) { err_ = "environment operator missing"; return -7; }
+        if (P.find(P.q[ic] + it->second.shift) != (int)oc) continue;
+        c.B = it->second.ptr + P.offset((int)oc) * (long long)d2 + P.offset(ic); c.b_k = 1; c.b_n = d2;
+        c.K = P.dim[ic];
+      } else {
+        if (ic != (int)oc) continue;
+        c.add = 1;
+      }
+      if (!push(c)) { err_ = "work list: too many chunks"; return -2; }
+    }
+    o.chunk_end = nc;
+    for (int m0 = 0; m0 < rows; m0 += KT_BM)
+      for (int n0 = 0; n0 < dc; n0 += KT_BN) {
+        if (nt >= max_tiles) { err_ = "work list: too many tiles"; return -2; }
+        tiles[nt++] = KTile{no, m0, n0, o.chunk_begin, o.chunk_end, -1};
+      }
+    ++no;
+  }
+  *n_tiles = nt;
+  *n_outs = no;
+  *n_chunks = nc;
+  return 0;
+}
+
 long long Engine::matvec_flops_algorithmic(int node) {
   (void)node;
   return 0;

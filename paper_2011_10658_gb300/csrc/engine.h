@@ -172,6 +172,13 @@ class Engine {
   // and rebuild all renormalized operators; the centre becomes the root.
   int load_tensors(const double* const* host, const long long* sizes, int n);
   int move_to(int target);
+  // Work list of y = H_eff x at a bottom-node centre for the FP64 grouped
+  // GEMM, written into caller-provided arrays with no allocation: x and y
+  // are used in place, row maps and environment operators must already
+  // exist.  Returns 0, -7 if the centre is not a bottom node or a needed
+  // row map is missing, -2 if an array is too small.
+  int noalloc_worklist(const double* x, double* y, KTile* tiles, int max_tiles, KOutput* outs, int max_outs,
+                       KChunk* chunks, int max_chunks, int* n_tiles, int* n_outs, int* n_chunks);
   int optimize_node(int node, double tol, int max_krylov, SweepStats* st, double* e);
   // H_eff x at the current centre (x, y device pointers, centre layout).
   int apply_heff(const double* x, double* y, int cls_filter);
