@@ -303,6 +303,7 @@ void Engine::ensure_scratch(long long elems) {
 
 void Engine::ensure_zpool(long long elems) {
   if (elems <= zpool_elems_) return;
+  clear_plan_caches();   // cached plans point into the old pool
   if (zpool_) { untrack(zpool_); cudaFree(zpool_); }
   zpool_elems_ = elems + elems / 4;
   cudaMalloc(&zpool_, zpool_elems_ * sizeof(double));
@@ -382,6 +383,58 @@ int Engine::run_plan(KPlan& pl) {
   return check(cudaGetLastError(), "kc_gemm launch") ? 0 : -3;
 }
 
+KPlan* Engine::cached_plan(int kind, int a, int b, int c, const std::function<void(KPlan&)>& build) {
+  const auto key = std::make_tuple(kind, a, b, c);
+  auto it = plan_cache_.find(key);
+  if (it != plan_cache_.end()) return it->second.get();
+  std::unique_ptr<KPlan> pl(new KPlan);
+  build(*pl);
+  pl->finalize(kKPart);
+  pl->upload(stream_);
+  KPlan* raw = pl.get();
+  plan_cache_[key] = std::move(pl);
+  return raw;
+}
+
+void Engine::cached_plans(int kind, int a, int b, int n, KPlan** out, const std::function<void(KPlan**)>& build) {
+  if (plan_cache_.find(std::make_tuple(kind, a, b, 0)) == plan_cache_.end()) {
+    std::unique_ptr<KPlan> pl[4];
+    KPlan* raw[4];
+    for (int i = 0; i < n; ++i) {
+      pl[i].reset(new KPlan);
+      raw[i] = pl[i].get();
+    }
+    build(raw);
+    for (int i = 0; i < n; ++i) {
+      raw[i]->finalize(kKPart);
+      raw[i]->upload(stream_);
+      plan_cache_[std::make_tuple(kind, a, b, i)] = std::move(pl[i]);
+    }
+  }
+  for (int i = 0; i < n; ++i) out[i] = plan_cache_.at(std::make_tuple(kind, a, b, i)).get();
+}
+
+int Engine::launch_plan(KPlan* pl, int fp32) {
+  if (pl->tiles.empty()) return 0;
+  ensure_scratch(std::max<long long>(pl->scratch_need, 1));
+  if (validate_ && !validate_plan(*pl, "plan")) return -1;
+  launch_kc_gemm(pl->d_tiles, (int)pl->tiles.size(), pl->d_outs, pl->d_chunks, scratch_, stream_, fp32);
+  launch_kc_reduce(pl->d_outs, (int)pl->outs.size(), pl->d_red, (int)pl->red.size(), scratch_, stream_);
+  return check(cudaGetLastError(), "kc_gemm launch") ? 0 : -3;
+}
+
+void Engine::clear_plan_caches() {
+  cudaStreamSynchronize(stream_);
+  plan_cache_.clear();
+  heff_cache_.clear();
+}
+
+void Engine::set_precision(int p) {
+  clear_tc_cache();
+  precision_ = p;
+  mixed_tol = p == PREC_TF32X3 ? 1e-7 : (p == PREC_TF32 ? 1e-5 : 1e-4);
+}
+
 Engine::Engine(const Params& p, int chi, uint64_t seed, int precision, cudaStream_t stream)
     : p_(p), chi_(chi), seed_(seed), precision_(precision), stream_(stream) {
   lat_ = Lattice{p.Lx, p.Ly, p.Lz};
@@ -415,6 +468,13 @@ Engine::Engine(const Params& p, int chi, uint64_t seed, int precision, cudaStrea
   d_partial_ = (double*)dalloc(304 * (kMaxKrylov + 2) * sizeof(double));
   d_err_ = (int*)dalloc(sizeof(int));
   cudaMemsetAsync(d_err_, 0, sizeof(int), stream_);
+  long long dmax = 1;
+  for (const Sectors& b : bonds_) dmax = std::max<long long>(dmax, b.total());
+  qr_G_ = (double*)dalloc(dmax * dmax * sizeof(double));
+  qr_Rinv_ = (double*)dalloc(dmax * dmax * sizeof(double));
+  qr_Racc_ = (double*)dalloc(dmax * dmax * sizeof(double));
+  qr_Rtmp_ = (double*)dalloc(dmax * dmax * sizeof(double));
+  move_R_ = (double*)dalloc(dmax * dmax * sizeof(double));
   mixed_tol = precision == PREC_TF32X3 ? 1e-7 : (precision == PREC_TF32 ? 1e-5 : 1e-4);
   init_tensors();
 }
@@ -422,9 +482,16 @@ Engine::Engine(const Params& p, int chi, uint64_t seed, int precision, cudaStrea
 Engine::~Engine() {
   cudaStreamSynchronize(stream_);
   for (auto& kv : site_ops_) delete kv.second;
-  for (int i = 0; i < 3; ++i) heff_stage_[i].release();
   work_.release();
-  tc_.release();
+  plan_cache_.clear();
+  heff_cache_.clear();
+  tc_cache_.clear();
+  for (auto& kv : qr_desc_) {
+    cudaFree(kv.second.off);
+    cudaFree(kv.second.n);
+    cudaFree(kv.second.ld);
+    cudaFree(kv.second.status);
+  }
   if (xstage_) cudaFree(xstage_);
   if (xstage32_) cudaFree(xstage32_);
   if (wbuf_) cudaFree(wbuf_);
@@ -657,106 +724,101 @@ void Engine::plan_contract_but(KPlan& pl, const Layout& LT, const double* T, con
 }
 
 // ------------------------------------------------------------------ QR
+enum PlanKind { PK_UP = 1, PK_DOWN = 2, PK_QR_GRAM = 3, PK_QR_APPLY = 4, PK_QR_RACC = 5, PK_ABSORB = 6 };
+
 // CholeskyQR2 of T[node] with `leg` as the column index, per sector of that
 // leg.  T <- Q.  If Rout != nullptr, R (dim x dim, block diagonal) is written.
+// An ill-conditioned or rank-deficient sector sends the whole leg to the
+// Gram-Schmidt fallback (qr_gram_schmidt).
 int Engine::qr_toward(int node, int leg, double* Rout) {
   const Layout& L = layout_[node];
   const Sectors& S = L.leg[leg];
   const int dim = S.total();
   const long long dd = (long long)dim * dim;
-  double* Gb = nullptr;
-  double* Rinv = nullptr;
-  double* Racc = nullptr;
-  double* Rtmp = nullptr;
-  cudaMalloc(&Gb, dd * sizeof(double));
-  cudaMalloc(&Rinv, dd * sizeof(double));
-  cudaMalloc(&Racc, dd * sizeof(double));
-  cudaMalloc(&Rtmp, dd * sizeof(double));
-  track(Gb, dd * sizeof(double));
-  track(Rinv, dd * sizeof(double));
-  track(Racc, dd * sizeof(double));
-  track(Rtmp, dd * sizeof(double));
-  std::vector<long long> off;
-  std::vector<int> nn, ld;
-  int max_n = 0;
-  for (size_t i = 0; i < S.q.size(); ++i) {
-    off.push_back(S.offset((int)i) * dim + S.offset((int)i));
-    nn.push_back(S.dim[i]);
-    ld.push_back(dim);
-    max_n = std::max(max_n, S.dim[i]);
+  double* Gb = qr_G_;
+  double* Rinv = qr_Rinv_;
+  double* Racc = qr_Racc_;
+  double* Rtmp = qr_Rtmp_;
+  auto dit = qr_desc_.find({node, leg});
+  if (dit == qr_desc_.end()) {
+    std::vector<long long> off;
+    std::vector<int> nn, ld;
+    QrDesc d;
+    for (size_t i = 0; i < S.q.size(); ++i) {
+      off.push_back(S.offset((int)i) * dim + S.offset((int)i));
+      nn.push_back(S.dim[i]);
+      ld.push_back(dim);
+      d.max_n = std::max(d.max_n, S.dim[i]);
+    }
+    d.count = (int)nn.size();
+    cudaMalloc(&d.off, off.size() * sizeof(long long));
+    cudaMalloc(&d.n, nn.size() * sizeof(int));
+    cudaMalloc(&d.ld, ld.size() * sizeof(int));
+    cudaMalloc(&d.status, nn.size() * sizeof(int));
+    cudaMemcpyAsync(d.off, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice, stream_);
+    cudaMemcpyAsync(d.n, nn.data(), nn.size() * sizeof(int), cudaMemcpyHostToDevice, stream_);
+    cudaMemcpyAsync(d.ld, ld.data(), ld.size() * sizeof(int), cudaMemcpyHostToDevice, stream_);
+    dit = qr_desc_.emplace(std::make_pair(node, leg), d).first;
   }
-  if (max_n > 160) {
+  const QrDesc& d = dit->second;
+  if (d.max_n > 160) {
     err_ = "sector dimension above 160 is not supported by the QR kernel";
     return -7;
   }
-  long long* d_off = nullptr;
-  int *d_n = nullptr, *d_ld = nullptr, *d_status = nullptr;
-  cudaMalloc(&d_off, off.size() * sizeof(long long));
-  cudaMalloc(&d_n, nn.size() * sizeof(int));
-  cudaMalloc(&d_ld, ld.size() * sizeof(int));
-  cudaMalloc(&d_status, nn.size() * sizeof(int));
-  cudaMemcpyAsync(d_off, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice, stream_);
-  cudaMemcpyAsync(d_n, nn.data(), nn.size() * sizeof(int), cudaMemcpyHostToDevice, stream_);
-  cudaMemcpyAsync(d_ld, ld.data(), ld.size() * sizeof(int), cudaMemcpyHostToDevice, stream_);
+  double* T = T_[node];
+  KPlan* gram = cached_plan(PK_QR_GRAM, node, leg, 0, [&](KPlan& pl) {
+    plan_contract_but(pl, L, T, L, T, leg, Gb, dim, 1.0);
+  });
+  KPlan* apply = cached_plan(PK_QR_APPLY, node, leg, 0, [&](KPlan& pl) {
+    plan_leg_apply(pl, L, T, L, tmp_, leg, Rinv, dim, 0, true, 1.0);
+  });
+  KPlan* racc = cached_plan(PK_QR_RACC, node, leg, 0, [&](KPlan& pl) {
+    for (size_t i = 0; i < S.q.size(); ++i) {
+      const long long o = S.offset((int)i);
+      pl.add_output(Rtmp + o * dim + o, dim, 1, S.dim[i], S.dim[i], 0);
+      KChunk c = make_chunk();
+      c.A = Gb + o * dim + o; c.a_m = dim; c.a_k = 1;
+      c.B = Racc + o * dim + o; c.b_k = dim; c.b_n = 1;
+      c.K = S.dim[i];
+      pl.add_chunk(c);
+    }
+  });
   int rc = 0;
   bool fallback = false;
   for (int pass = 0; pass < 2 && rc == 0; ++pass) {
     cudaMemsetAsync(Gb, 0, dd * sizeof(double), stream_);
-    work_.clear();
-    plan_contract_but(work_, L, T_[node], L, T_[node], leg, Gb, dim, 1.0);
-    rc = run_plan(work_);
+    rc = launch_plan(gram);
     if (rc) break;
     cudaMemsetAsync(Rinv, 0, dd * sizeof(double), stream_);
-    launch_cholesky_inv(Gb, Rinv, d_off, d_n, d_ld, (int)nn.size(), max_n, kQrFallback * kQrFallback, d_status,
-                        stream_);
-    std::vector<int> status(nn.size());
-    cudaMemcpyAsync(status.data(), d_status, nn.size() * sizeof(int), cudaMemcpyDeviceToHost, stream_);
+    launch_cholesky_inv(Gb, Rinv, d.off, d.n, d.ld, d.count, d.max_n, kQrFallback * kQrFallback, d.status, stream_);
+    std::vector<int> status(d.count);
+    cudaMemcpyAsync(status.data(), d.status, d.count * sizeof(int), cudaMemcpyDeviceToHost, stream_);
     if (!check(cudaStreamSynchronize(stream_), "cholesky")) { rc = -3; break; }
     for (int st : status)
       if (st) fallback = true;
     if (fallback) {
       if (pass == 0) break;
-      // second pass of a well-conditioned first pass cannot be ill-conditioned
+      // a second pass of a well-conditioned first pass cannot be ill-conditioned
       err_ = "CholeskyQR: second pass lost positive definiteness";
       rc = -5;
       break;
     }
     // T <- T (x)_leg Rinv^T  (Q = X R^{-1})
     cudaMemsetAsync(tmp_, 0, L.size * sizeof(double), stream_);
-    work_.clear();
-    plan_leg_apply(work_, L, T_[node], L, tmp_, leg, Rinv, dim, 0, true, 1.0);
-    rc = run_plan(work_);
+    rc = launch_plan(apply);
     if (rc) break;
-    launch_copy(tmp_, T_[node], L.size, stream_);
-    // R accumulation: Racc = R_pass * Racc (R in Gb, upper)
-    if (Rout) {
-      if (pass == 0) {
-        cudaMemcpyAsync(Racc, Gb, dd * sizeof(double), cudaMemcpyDeviceToDevice, stream_);
-      } else {
-        cudaMemsetAsync(Rtmp, 0, dd * sizeof(double), stream_);
-        work_.clear();
-        for (size_t i = 0; i < S.q.size(); ++i) {
-          const long long o = S.offset((int)i);
-          work_.add_output(Rtmp + o * dim + o, dim, 1, S.dim[i], S.dim[i], 0);
-          KChunk c = make_chunk();
-          c.A = Gb + o * dim + o; c.a_m = dim; c.a_k = 1;
-          c.B = Racc + o * dim + o; c.b_k = dim; c.b_n = 1;
-          c.K = S.dim[i];
-          work_.add_chunk(c);
-        }
-        rc = run_plan(work_);
-        cudaMemcpyAsync(Racc, Rtmp, dd * sizeof(double), cudaMemcpyDeviceToDevice, stream_);
-      }
+    launch_copy(tmp_, T, L.size, stream_);
+    // R accumulation: Racc = R_pass * Racc (R of this pass in Gb, upper)
+    if (pass == 0) {
+      cudaMemcpyAsync(Racc, Gb, dd * sizeof(double), cudaMemcpyDeviceToDevice, stream_);
+    } else {
+      cudaMemsetAsync(Rtmp, 0, dd * sizeof(double), stream_);
+      rc = launch_plan(racc);
+      cudaMemcpyAsync(Racc, Rtmp, dd * sizeof(double), cudaMemcpyDeviceToDevice, stream_);
     }
   }
   if (rc == 0 && fallback) rc = qr_gram_schmidt(node, leg, Racc);
   if (rc == 0 && Rout) cudaMemcpyAsync(Rout, Racc, dd * sizeof(double), cudaMemcpyDeviceToDevice, stream_);
-  cudaStreamSynchronize(stream_);
-  for (double* b : {Gb, Rinv, Racc, Rtmp}) { untrack(b); cudaFree(b); }
-  cudaFree(d_off);
-  cudaFree(d_n);
-  cudaFree(d_ld);
-  cudaFree(d_status);
   return rc;
 }
 
@@ -885,14 +947,15 @@ int Engine::qr_gram_schmidt(int node, int leg, double* Rout) {
   return rc;
 }
 
-// T[node] <- R (x)_leg T[node]
+// T[node] <- R (x)_leg T[node]  (R is always the move buffer)
 int Engine::absorb(int node, int leg, const double* R) {
   const Layout& L = layout_[node];
   const int dim = L.leg[leg].total();
+  KPlan* pl = cached_plan(PK_ABSORB, node, leg, 0, [&](KPlan& p) {
+    plan_leg_apply(p, L, T_[node], L, tmp_, leg, R, dim, 0, false, 1.0);
+  });
   cudaMemsetAsync(tmp_, 0, L.size * sizeof(double), stream_);
-  work_.clear();
-  plan_leg_apply(work_, L, T_[node], L, tmp_, leg, R, dim, 0, false, 1.0);
-  int rc = run_plan(work_);
+  int rc = launch_plan(pl);
   launch_copy(tmp_, T_[node], L.size, stream_);
   return rc;
 }
@@ -952,29 +1015,30 @@ int Engine::compute_up(int node) {
   }
   for (int c = 0; c < N_CLASSES; ++c) cudaMemsetAsync(out.H[c], 0, dd * sizeof(double), stream_);
   for (auto& kv : out.term) cudaMemsetAsync(kv.second.ptr, 0, dd * sizeof(double), stream_);
-  work_.clear();
   int rc = 0;
   if (bottom) {
     // term contributions through row maps: O[c', c] += alpha sum_r T[r, c'] val(r) T[map(r), c]
-    auto add_map = [&](double* O, double alpha, const std::vector<RowMap>& maps) {
-      for (size_t oc = 0; oc < maps.size(); ++oc) {
-        const RowMap& rm = maps[oc];
-        if (rm.src_sector < 0 || L.sec_rows[oc] == 0) continue;
-        const int ic = rm.src_sector;
-        work_.add_output(O + L.leg[2].offset((int)oc) * dim + L.leg[2].offset(ic), dim, 1, L.leg[2].dim[oc],
-                         L.leg[2].dim[ic], 1);
-        KChunk c = make_chunk();
-        c.A = T + L.sec_off[oc]; c.a_m = 1; c.a_k = L.leg[2].dim[oc];
-        c.B = T + L.sec_off[ic]; c.b_k = L.leg[2].dim[ic]; c.b_n = 1;
-        c.bmap = rm.map; c.bval = rm.val;
-        c.K = L.sec_rows[oc]; c.alpha = alpha;
-        work_.add_chunk(c);
-      }
-    };
-    for (const Contrib& c : cs) add_map(c.O, c.alpha, rowmap(node, c.term));
-    for (int leg = 0; leg < 2; ++leg)
-      for (int cl = 0; cl < N_CLASSES; ++cl) add_map(out.H[cl], 1.0, site_ham_map(node, leg, cl));
-    rc = run_plan(work_);
+    KPlan* pl = cached_plan(PK_UP, node, 0, 0, [&](KPlan& w) {
+      auto add_map = [&](double* O, double alpha, const std::vector<RowMap>& maps) {
+        for (size_t oc = 0; oc < maps.size(); ++oc) {
+          const RowMap& rm = maps[oc];
+          if (rm.src_sector < 0 || L.sec_rows[oc] == 0) continue;
+          const int ic = rm.src_sector;
+          w.add_output(O + L.leg[2].offset((int)oc) * dim + L.leg[2].offset(ic), dim, 1, L.leg[2].dim[oc],
+                       L.leg[2].dim[ic], 1);
+          KChunk c = make_chunk();
+          c.A = T + L.sec_off[oc]; c.a_m = 1; c.a_k = L.leg[2].dim[oc];
+          c.B = T + L.sec_off[ic]; c.b_k = L.leg[2].dim[ic]; c.b_n = 1;
+          c.bmap = rm.map; c.bval = rm.val;
+          c.K = L.sec_rows[oc]; c.alpha = alpha;
+          w.add_chunk(c);
+        }
+      };
+      for (const Contrib& c : cs) add_map(c.O, c.alpha, rowmap(node, c.term));
+      for (int leg = 0; leg < 2; ++leg)
+        for (int cl = 0; cl < N_CLASSES; ++cl) add_map(out.H[cl], 1.0, site_ham_map(node, leg, cl));
+    });
+    rc = launch_plan(pl);
   } else {
     // upper node: Z = (A (x) B) T into pool buffers, then O += T^T Z
     struct Job { double* O; double alpha; int shA, shB; const double* A; const double* B; };
@@ -1006,41 +1070,36 @@ int Engine::compute_up(int node) {
     std::map<int, Layout> lays;
     for (int s = -2; s <= 2; ++s) lays[s] = shifted(node, s);
     const int dl = L.leg[0].total(), dr = L.leg[1].total();
-    for (size_t j0 = 0; j0 < jobs.size() && rc == 0; j0 += batch) {
-      size_t j1 = std::min(jobs.size(), j0 + batch);
+    for (size_t j0 = 0, bi = 0; j0 < jobs.size() && rc == 0; j0 += batch, ++bi) {
+      const size_t j1 = std::min(jobs.size(), j0 + batch);
       cudaMemsetAsync(zpool_, 0, 2 * batch * zsize * sizeof(double), stream_);
-      KPlan& s1 = heff_stage_[0];
-      KPlan& s2 = heff_stage_[1];
-      s1.clear();
-      s2.clear();
-      work_.clear();
-      for (size_t j = j0; j < j1; ++j) {
-        const Job& jb = jobs[j];
-        double* z1 = zpool_ + (2 * (j - j0)) * zsize;
-        double* z2 = z1 + zsize;
-        const double* Z = nullptr;
-        int shift = 0;
-        if (jb.A && jb.B) {
-          plan_leg_apply(s1, L, T, lays[jb.shA], z1, 0, jb.A, dl, jb.shA, false, 1.0);
-          plan_leg_apply(s2, lays[jb.shA], z1, lays[jb.shA + jb.shB], z2, 1, jb.B, dr, jb.shB, false, 1.0);
-          Z = z2;
-          shift = jb.shA + jb.shB;
-        } else if (jb.A) {
-          plan_leg_apply(s1, L, T, lays[jb.shA], z1, 0, jb.A, dl, jb.shA, false, 1.0);
-          Z = z1;
-          shift = jb.shA;
-        } else {
-          plan_leg_apply(s1, L, T, lays[jb.shB], z1, 1, jb.B, dr, jb.shB, false, 1.0);
-          Z = z1;
-          shift = jb.shB;
+      KPlan* st[3];
+      cached_plans(PK_UP, node, (int)bi + 1, 3, st, [&](KPlan** p) {
+        for (size_t j = j0; j < j1; ++j) {
+          const Job& jb = jobs[j];
+          double* z1 = zpool_ + (2 * (j - j0)) * zsize;
+          double* z2 = z1 + zsize;
+          const double* Z = nullptr;
+          int shift = 0;
+          if (jb.A && jb.B) {
+            plan_leg_apply(*p[0], L, T, lays[jb.shA], z1, 0, jb.A, dl, jb.shA, false, 1.0);
+            plan_leg_apply(*p[1], lays[jb.shA], z1, lays[jb.shA + jb.shB], z2, 1, jb.B, dr, jb.shB, false, 1.0);
+            Z = z2;
+            shift = jb.shA + jb.shB;
+          } else if (jb.A) {
+            plan_leg_apply(*p[0], L, T, lays[jb.shA], z1, 0, jb.A, dl, jb.shA, false, 1.0);
+            Z = z1;
+            shift = jb.shA;
+          } else {
+            plan_leg_apply(*p[0], L, T, lays[jb.shB], z1, 1, jb.B, dr, jb.shB, false, 1.0);
+            Z = z1;
+            shift = jb.shB;
+          }
+          plan_contract_but(*p[2], L, T, lays[shift], Z, 2, jb.O, dim, jb.alpha);
         }
-        plan_contract_but(work_, L, T, lays[shift], Z, 2, jb.O, dim, jb.alpha);
-      }
-      rc = run_plan(s1);
-      if (!rc && !s2.outs.empty()) rc = run_plan(s2);
-      if (!rc) rc = run_plan(work_);
+      });
+      for (int i = 0; i < 3 && rc == 0; ++i) rc = launch_plan(st[i]);
     }
-    plan_node_ = -1;   // stage plans reused: invalidate the H_eff cache
   }
   // Htot = sum of classes
   cudaMemsetAsync(out.Htot, 0, dd * sizeof(double), stream_);
@@ -1114,42 +1173,37 @@ int Engine::compute_down(int node) {
   const int ds = L.leg[sib_leg].total(), dp = L.leg[2].total();
   const double* T = T_[par];
   int rc = 0;
-  for (size_t j0 = 0; j0 < jobs.size() && rc == 0; j0 += batch) {
-    size_t j1 = std::min(jobs.size(), j0 + batch);
+  for (size_t j0 = 0, bi = 0; j0 < jobs.size() && rc == 0; j0 += batch, ++bi) {
+    const size_t j1 = std::min(jobs.size(), j0 + batch);
     cudaMemsetAsync(zpool_, 0, 2 * batch * zsize * sizeof(double), stream_);
-    KPlan& s1 = heff_stage_[0];
-    KPlan& s2 = heff_stage_[1];
-    s1.clear();
-    s2.clear();
-    work_.clear();
-    for (size_t j = j0; j < j1; ++j) {
-      const Job& jb = jobs[j];
-      double* z1 = zpool_ + (2 * (j - j0)) * zsize;
-      double* z2 = z1 + zsize;
-      const double* Z;
-      int shift;
-      // sibling op on sib_leg: layout shift += shS; parent-leg op: shift -= shP
-      if (jb.S && jb.P) {
-        plan_leg_apply(s1, L, T, lays[jb.shS], z1, sib_leg, jb.S, ds, jb.shS, false, 1.0);
-        plan_leg_apply(s2, lays[jb.shS], z1, lays[jb.shS - jb.shP], z2, 2, jb.P, dp, jb.shP, false, 1.0);
-        Z = z2;
-        shift = jb.shS - jb.shP;
-      } else if (jb.S) {
-        plan_leg_apply(s1, L, T, lays[jb.shS], z1, sib_leg, jb.S, ds, jb.shS, false, 1.0);
-        Z = z1;
-        shift = jb.shS;
-      } else {
-        plan_leg_apply(s1, L, T, lays[-jb.shP], z1, 2, jb.P, dp, jb.shP, false, 1.0);
-        Z = z1;
-        shift = -jb.shP;
+    KPlan* st[3];
+    cached_plans(PK_DOWN, node, (int)bi, 3, st, [&](KPlan** p) {
+      for (size_t j = j0; j < j1; ++j) {
+        const Job& jb = jobs[j];
+        double* z1 = zpool_ + (2 * (j - j0)) * zsize;
+        double* z2 = z1 + zsize;
+        const double* Z;
+        int shift;
+        // sibling op on sib_leg: layout shift += shS; parent-leg op: shift -= shP
+        if (jb.S && jb.P) {
+          plan_leg_apply(*p[0], L, T, lays[jb.shS], z1, sib_leg, jb.S, ds, jb.shS, false, 1.0);
+          plan_leg_apply(*p[1], lays[jb.shS], z1, lays[jb.shS - jb.shP], z2, 2, jb.P, dp, jb.shP, false, 1.0);
+          Z = z2;
+          shift = jb.shS - jb.shP;
+        } else if (jb.S) {
+          plan_leg_apply(*p[0], L, T, lays[jb.shS], z1, sib_leg, jb.S, ds, jb.shS, false, 1.0);
+          Z = z1;
+          shift = jb.shS;
+        } else {
+          plan_leg_apply(*p[0], L, T, lays[-jb.shP], z1, 2, jb.P, dp, jb.shP, false, 1.0);
+          Z = z1;
+          shift = -jb.shP;
+        }
+        plan_contract_but(*p[2], L, T, lays[shift], Z, leg, jb.O, dim, jb.alpha);
       }
-      plan_contract_but(work_, L, T, lays[shift], Z, leg, jb.O, dim, jb.alpha);
-    }
-    rc = run_plan(s1);
-    if (!rc && !s2.outs.empty()) rc = run_plan(s2);
-    if (!rc) rc = run_plan(work_);
+    });
+    for (int i = 0; i < 3 && rc == 0; ++i) rc = launch_plan(st[i]);
   }
-  plan_node_ = -1;
   cudaMemsetAsync(out.Htot, 0, dd * sizeof(double), stream_);
   for (int c = 0; c < N_CLASSES; ++c) launch_add_scaled(out.H[c], out.Htot, dd, 1.0, stream_);
   return rc;
@@ -1188,19 +1242,11 @@ int Engine::move_path(int target) {
       leg_t = 2;
       leg_c = (nodes_[c].child_kind[0] == 1 && nodes_[c].child[0] == t) ? 0 : 1;
     }
-    const int dim = layout_[c].leg[leg_c].total();
-    double* R = nullptr;
-    cudaMalloc(&R, (size_t)dim * dim * sizeof(double));
-    track(R, (size_t)dim * dim * sizeof(double));
-    int rc = qr_toward(c, leg_c, R);
-    if (!rc) rc = absorb(t, leg_t, R);
-    cudaStreamSynchronize(stream_);
-    untrack(R);
-    cudaFree(R);
+    int rc = qr_toward(c, leg_c, move_R_);
+    if (!rc) rc = absorb(t, leg_t, move_R_);
     if (rc) return rc;
     center_ = t;
-    tc_node_ = -1;
-    plan_node_ = -1;
+    tc_w_node_ = -1;   // environment operators change with the move
     if (leg_c == 2) rc = compute_up(c);
     else rc = compute_down(t);
     if (rc) return rc;
@@ -1276,14 +1322,19 @@ void Engine::build_heff_terms(int node, int cls, std::vector<HTerm>* out) {
   }
 }
 
-int Engine::build_heff_plan(int node, int cls) {
-  if (plan_node_ == node && plan_cls_ == cls) return 0;
+// H_eff plans of (node, class filter), built on first use and replayed.
+// Returns nullptr (err_ set) if validation fails.
+Engine::HeffPlans* Engine::heff_plans(int node, int cls) {
+  const auto key = std::make_pair(node, cls);
+  auto hit = heff_cache_.find(key);
+  if (hit != heff_cache_.end()) return hit->second.get();
+  std::unique_ptr<HeffPlans> hp(new HeffPlans);
+  KPlan* st = hp->st;
   std::vector<HTerm> hts;
   build_heff_terms(node, cls, &hts);
   const Layout& L = layout_[node];
   const bool bottom = nodes_[node].child_kind[0] == 0;
-  for (int i = 0; i < 3; ++i) heff_stage_[i].clear();
-  KPlan& s3 = heff_stage_[2];
+  KPlan& s3 = st[2];
   const int d2 = L.leg[2].total();
   const double cst = (cls < 0 || cls == CLS_NU) ? constant_ : 0.0;
   if (bottom) {
@@ -1338,7 +1389,7 @@ int Engine::build_heff_plan(int node, int cls) {
     int nz = 0;
     for (const HTerm& h : hts) nz += (h.op[0].kind ? 1 : 0) + (h.op[1].kind ? 1 : 0);
     ensure_zpool(std::max(1, nz) * zsize);
-    heff_z_elems_ = (long long)nz * zsize;
+    hp->z_elems = (long long)nz * zsize;
     const int dl = L.leg[0].total(), dr = L.leg[1].total();
     struct Src { const double* Z; int shift; };
     std::vector<Src> srcs;
@@ -1348,20 +1399,20 @@ int Engine::build_heff_plan(int node, int cls) {
       int shift = 0;
       if (h.op[0].kind) {
         double* z1 = zpool_ + (zi++) * zsize;
-        plan_leg_apply(heff_stage_[0], L, x_in_, lays[h.op[0].shift], z1, 0, h.op[0].ptr, dl, h.op[0].shift, false,
+        plan_leg_apply(st[0], L, x_in_, lays[h.op[0].shift], z1, 0, h.op[0].ptr, dl, h.op[0].shift, false,
                        1.0);
         Z = z1;
         shift = h.op[0].shift;
         if (h.op[1].kind) {
           double* z2 = zpool_ + (zi++) * zsize;
-          plan_leg_apply(heff_stage_[1], lays[shift], z1, lays[shift + h.op[1].shift], z2, 1, h.op[1].ptr, dr,
+          plan_leg_apply(st[1], lays[shift], z1, lays[shift + h.op[1].shift], z2, 1, h.op[1].ptr, dr,
                          h.op[1].shift, false, 1.0);
           Z = z2;
           shift += h.op[1].shift;
         }
       } else if (h.op[1].kind) {
         double* z1 = zpool_ + (zi++) * zsize;
-        plan_leg_apply(heff_stage_[0], L, x_in_, lays[h.op[1].shift], z1, 1, h.op[1].ptr, dr, h.op[1].shift, false,
+        plan_leg_apply(st[0], L, x_in_, lays[h.op[1].shift], z1, 1, h.op[1].ptr, dr, h.op[1].shift, false,
                        1.0);
         Z = z1;
         shift = h.op[1].shift;
@@ -1398,21 +1449,23 @@ int Engine::build_heff_plan(int node, int cls) {
         s3.add_chunk(c);
       }
     }
-    for (int i = 0; i < 2; ++i) heff_stage_[i].finalize(kKPart);
+    for (int i = 0; i < 2; ++i) st[i].finalize(kKPart);
   }
   s3.finalize(kKPart);
-  long long need = 0;
   for (int i = 0; i < 3; ++i) {
-    need = std::max(need, heff_stage_[i].scratch_need);
-    heff_stage_[i].upload(stream_);
+    hp->scratch_need = std::max(hp->scratch_need, st[i].scratch_need);
+    st[i].upload(stream_);
+    for (const KOutput& o : st[i].outs)
+      for (int c = o.chunk_begin; c < o.chunk_end; ++c)
+        if (!st[i].chunks[c].add) hp->flops += 2.0 * o.M * o.N * st[i].chunks[c].K;
   }
-  ensure_scratch(std::max<long long>(need, 1));
   if (validate_)
     for (int i = 0; i < 3; ++i)
-      if (!validate_plan(heff_stage_[i], "H_eff plan")) return -1;
-  plan_node_ = node;
-  plan_cls_ = cls;
-  return check(cudaGetLastError(), "plan") ? 0 : -3;
+      if (!validate_plan(st[i], "H_eff plan")) return nullptr;
+  if (!check(cudaGetLastError(), "plan")) return nullptr;
+  HeffPlans* raw = hp.get();
+  heff_cache_[key] = std::move(hp);
+  return raw;
 }
 
 bool Engine::mixed_node(int node) const {
@@ -1430,28 +1483,24 @@ int Engine::apply_heff(const double* x, double* y, int cls) {
     if (y != y_out_) launch_copy(y_out_, y, n, stream_);
     return check(cudaGetLastError(), "apply_heff (mixed)") ? 0 : -3;
   }
-  int rc = build_heff_plan(center_, cls);
-  if (rc) return rc;
+  HeffPlans* hp = heff_plans(center_, cls);
+  if (!hp) return -1;
+  ensure_scratch(std::max<long long>(hp->scratch_need, 1));
   if (x != x_in_) launch_copy(x, x_in_, n, stream_);
   cudaEvent_t e0 = nullptr;
   if (profiling_) ev_begin(&e0);
-  if (!bottom && heff_z_elems_ > 0) {
+  if (!bottom && hp->z_elems > 0) {
     // Z blocks that no source block maps to must read as zero
-    cudaMemsetAsync(zpool_, 0, heff_z_elems_ * sizeof(double), stream_);
+    cudaMemsetAsync(zpool_, 0, hp->z_elems * sizeof(double), stream_);
   }
-  double flops = 0.0;
   const int fp32 = (use_mixed_ && cls < 0) ? 1 : 0;
   for (int i = 0; i < 3; ++i) {
-    KPlan& pl = heff_stage_[i];
+    KPlan& pl = hp->st[i];
     if (pl.tiles.empty()) continue;
     launch_kc_gemm(pl.d_tiles, (int)pl.tiles.size(), pl.d_outs, pl.d_chunks, scratch_, stream_, fp32);
     launch_kc_reduce(pl.d_outs, (int)pl.outs.size(), pl.d_red, (int)pl.red.size(), scratch_, stream_);
-    if (profiling_)
-      for (const KOutput& o : pl.outs)
-        for (int c = o.chunk_begin; c < o.chunk_end; ++c)
-          if (!pl.chunks[c].add) flops += 2.0 * o.M * o.N * pl.chunks[c].K;
   }
-  if (profiling_) ev_end(e0, bottom ? KC_HEFF_SIMT_BOTTOM : KC_HEFF_SIMT_UPPER, flops, flops, 0.0);
+  if (profiling_) ev_end(e0, bottom ? KC_HEFF_SIMT_BOTTOM : KC_HEFF_SIMT_UPPER, hp->flops, hp->flops, 0.0);
   if (y != y_out_) launch_copy(y_out_, y, n, stream_);
   return check(cudaGetLastError(), "apply_heff") ? 0 : -3;
 }
@@ -1461,8 +1510,9 @@ int Engine::apply_heff(const double* x, double* y, int cls) {
 // environment block Hamiltonian) become GEMM chunks with their operator
 // blocks converted to BF16 / FP32 and scaled by the term coefficient; terms
 // acting on the two sites only, and the constant, are FP64 epilogue adds.
-int Engine::build_tc_plan(int node) {
-  if (tc_node_ == node) return 0;
+TcPlan* Engine::tc_plan(int node) {
+  auto cit = tc_cache_.find(node);
+  if (cit != tc_cache_.end()) return cit->second.get();
   std::vector<HTerm> hts;
   build_heff_terms(node, -1, &hts);
   const Layout& L = layout_[node];
@@ -1473,7 +1523,8 @@ int Engine::build_tc_plan(int node) {
   const bool split = precision_ == PREC_TF32X3;
   const int xmul = split ? 2 : 1;   // staged row width in units of kpad
   const int kmul = split ? 2 : 1;   // staged B row width in units of kpad
-  tc_.clear();
+  std::unique_ptr<TcPlan> tp(new TcPlan);
+  TcPlan& tc = *tp;
   std::vector<long long> soff(ns, 0);
   std::vector<int> kpad(ns);
   long long xs = 0;
@@ -1484,12 +1535,13 @@ int Engine::build_tc_plan(int node) {
   }
   // operand staging holds xmul * xs elements; an FP32 copy (xs) serves the epilogue
   if (xs > xstage_elems_) {
+    clear_tc_cache();   // cached plans point into the old staging
     if (xstage_) { untrack(xstage_); cudaFree(xstage_); }
     if (xstage32_) { untrack(xstage32_); cudaFree(xstage32_); xstage32_ = nullptr; }
     xstage_elems_ = xs + xs / 4;
-    if (!check(cudaMalloc(&xstage_, 2 * xstage_elems_ * elem), "x staging")) return -2;
+    if (!check(cudaMalloc(&xstage_, 2 * xstage_elems_ * elem), "x staging")) return nullptr;
     track(xstage_, 2 * xstage_elems_ * elem);
-    if (!check(cudaMalloc(&xstage32_, xstage_elems_ * 4), "x staging")) return -2;
+    if (!check(cudaMalloc(&xstage32_, xstage_elems_ * 4), "x staging")) return nullptr;
     track(xstage32_, xstage_elems_ * 4);
   }
   float* x32 = xstage32_;
@@ -1505,8 +1557,8 @@ int Engine::build_tc_plan(int node) {
     j.cols = P.dim[i];
     j.kpad = kpad[i];
     j.scale = 1.0;
-    tc_.xjobs.push_back(j);
-    tc_.x_max_elems = std::max(tc_.x_max_elems, (long long)j.rows * j.kpad);
+    tc.xjobs.push_back(j);
+    tc.x_max_elems = std::max(tc.x_max_elems, (long long)j.rows * j.kpad);
   }
   // W slots
   long long wtot = 0;
@@ -1521,9 +1573,9 @@ int Engine::build_tc_plan(int node) {
     o.rows = rows;
     o.n = P.dim[oc];
     o.npad = kpad[oc];
-    o.chunk_begin = (int)tc_.chunks.size();
-    o.add_begin = (int)tc_.adds.size();
-    tc_.max_npad = std::max(tc_.max_npad, o.npad);
+    o.chunk_begin = (int)tc.chunks.size();
+    o.add_begin = (int)tc.adds.size();
+    tc.max_npad = std::max(tc.max_npad, o.npad);
     if (cst != 0.0) {
       TcAdd a;
       a.X32 = x32 + soff[oc];
@@ -1531,7 +1583,7 @@ int Engine::build_tc_plan(int node) {
       a.val = nullptr;
       a.alpha = cst;
       a.ld = kpad[oc];
-      tc_.adds.push_back(a);
+      tc.adds.push_back(a);
     }
     for (const HTerm& h : hts) {
       const bool phys = h.op[0].kind == 2 || h.op[1].kind == 2;
@@ -1545,7 +1597,10 @@ int Engine::build_tc_plan(int node) {
       const int ic = phys ? rm->src_sector : oc;
       if (h.op[2].kind == 1) {
         if (P.find(P.q[ic] + h.op[2].shift) != oc) continue;
-        if (rm && rm->val) return -7;   // GEMM terms carry +-1 maps only
+        if (rm && rm->val) {   // GEMM terms carry +-1 maps only
+          err_ = "tensor-core plan: valued row map on an environment term";
+          return nullptr;
+        }
         TcChunk c;
         c.X = (char*)xstage_ + xmul * soff[ic] * elem;
         c.map = rm ? rm->map : nullptr;
@@ -1555,11 +1610,11 @@ int Engine::build_tc_plan(int node) {
         wj.push_back({oc, ic, h.op[2].ptr, h.coef, wtot});
         c.W = (const void*)(intptr_t)wtot;   // patched below once the buffer exists
         wtot += welems;
-        tc_.chunks.push_back(c);
-        tc_.max_kpad = std::max(tc_.max_kpad, c.kpad);
+        tc.chunks.push_back(c);
+        tc.max_kpad = std::max(tc.max_kpad, c.kpad);
         const double nnz = rm ? (double)rm->nnz : (double)rows;
-        tc_.flops_alg += 2.0 * nnz * P.dim[oc] * P.dim[ic];
-        tc_.flops_exec += 2.0 * ((rows + 127) / 128 * 128) * o.npad * kpad[ic] * (split ? 3 : 1);
+        tc.flops_alg += 2.0 * nnz * P.dim[oc] * P.dim[ic];
+        tc.flops_exec += 2.0 * ((rows + 127) / 128 * 128) * o.npad * kpad[ic] * (split ? 3 : 1);
       } else {
         if (ic != oc) continue;
         TcAdd a;
@@ -1568,22 +1623,23 @@ int Engine::build_tc_plan(int node) {
         a.val = rm ? rm->val : nullptr;
         a.alpha = h.coef;
         a.ld = kpad[ic];
-        tc_.adds.push_back(a);
+        tc.adds.push_back(a);
       }
     }
-    o.chunk_end = (int)tc_.chunks.size();
-    o.add_end = (int)tc_.adds.size();
-    tc_.outs.push_back(o);
-    for (int r0 = 0; r0 < rows; r0 += 128) tc_.tiles.push_back({(int)tc_.outs.size() - 1, r0});
+    o.chunk_end = (int)tc.chunks.size();
+    o.add_end = (int)tc.adds.size();
+    tc.outs.push_back(o);
+    for (int r0 = 0; r0 < rows; r0 += 128) tc.tiles.push_back({(int)tc.outs.size() - 1, r0});
   }
   if (wtot > wbuf_elems_) {
+    clear_tc_cache();   // cached plans point into the old W buffer
     if (wbuf_) { untrack(wbuf_); cudaFree(wbuf_); }
     wbuf_elems_ = wtot + wtot / 4 + 1024;
-    if (!check(cudaMalloc(&wbuf_, wbuf_elems_ * elem), "W staging")) return -2;
+    if (!check(cudaMalloc(&wbuf_, wbuf_elems_ * elem), "W staging")) return nullptr;
     track(wbuf_, wbuf_elems_ * elem);
   }
-  for (TcChunk& c : tc_.chunks) c.W = (char*)wbuf_ + (intptr_t)c.W * elem;
-  if (wtot > 0) cudaMemsetAsync(wbuf_, 0, wtot * elem, stream_);
+  for (TcChunk& c : tc.chunks) c.W = (char*)wbuf_ + (intptr_t)c.W * elem;
+  tc.wtot = wtot;
   for (const WJ& w : wj) {
     ConvJob j;
     j.src = w.op + P.offset(w.oc) * (long long)d2 + P.offset(w.ic);
@@ -1595,37 +1651,50 @@ int Engine::build_tc_plan(int node) {
     j.cols = P.dim[w.ic];
     j.kpad = kpad[w.ic];
     j.scale = w.coef;
-    tc_.wjobs.push_back(j);
-    tc_.w_max_elems = std::max(tc_.w_max_elems, (long long)j.rows * j.kpad);
+    tc.wjobs.push_back(j);
+    tc.w_max_elems = std::max(tc.w_max_elems, (long long)j.rows * j.kpad);
   }
   // algorithmic bytes: x staging read once, y written once (FP64), W read once
-  tc_.bytes_alg = (double)xs * xmul * elem + (double)L.size * 8.0 + (double)wtot * elem;
-  grow_upload(tc_.d_tiles, tc_.cap[0], tc_.tiles, stream_);
-  grow_upload(tc_.d_outs, tc_.cap[1], tc_.outs, stream_);
-  grow_upload(tc_.d_chunks, tc_.cap[2], tc_.chunks, stream_);
-  grow_upload(tc_.d_adds, tc_.cap[3], tc_.adds, stream_);
-  grow_upload(tc_.d_xjobs, tc_.cap[4], tc_.xjobs, stream_);
-  grow_upload(tc_.d_wjobs, tc_.cap[5], tc_.wjobs, stream_);
-  launch_convert(elem, split ? 2 : 0, tc_.d_wjobs, (int)tc_.wjobs.size(), tc_.w_max_elems, stream_);
-  tc_node_ = node;
-  return check(cudaGetLastError(), "tc plan") ? 0 : -3;
+  tc.bytes_alg = (double)xs * xmul * elem + (double)L.size * 8.0 + (double)wtot * elem;
+  grow_upload(tc.d_tiles, tc.cap[0], tc.tiles, stream_);
+  grow_upload(tc.d_outs, tc.cap[1], tc.outs, stream_);
+  grow_upload(tc.d_chunks, tc.cap[2], tc.chunks, stream_);
+  grow_upload(tc.d_adds, tc.cap[3], tc.adds, stream_);
+  grow_upload(tc.d_xjobs, tc.cap[4], tc.xjobs, stream_);
+  grow_upload(tc.d_wjobs, tc.cap[5], tc.wjobs, stream_);
+  if (!check(cudaGetLastError(), "tc plan")) return nullptr;
+  TcPlan* raw = tp.get();
+  tc_cache_[node] = std::move(tp);
+  return raw;
+}
+
+void Engine::clear_tc_cache() {
+  cudaStreamSynchronize(stream_);
+  tc_cache_.clear();
+  tc_w_node_ = -1;
 }
 
 int Engine::apply_heff_mixed() {
-  int rc = build_tc_plan(center_);
-  if (rc) return rc;
+  TcPlan* tc = tc_plan(center_);
+  if (!tc) return -1;
   const int elem = precision_ == PREC_BF16 ? 2 : 4;
   const int split = precision_ == PREC_TF32X3 ? 1 : 0;
-  launch_convert(elem, split, tc_.d_xjobs, (int)tc_.xjobs.size(), tc_.x_max_elems, stream_);
+  if (tc_w_node_ != center_) {
+    // environment blocks of this centre (padding zero) into the shared W buffer
+    if (tc->wtot > 0) cudaMemsetAsync(wbuf_, 0, tc->wtot * elem, stream_);
+    launch_convert(elem, split ? 2 : 0, tc->d_wjobs, (int)tc->wjobs.size(), tc->w_max_elems, stream_);
+    tc_w_node_ = center_;
+  }
+  launch_convert(elem, split, tc->d_xjobs, (int)tc->xjobs.size(), tc->x_max_elems, stream_);
   cudaEvent_t e0 = nullptr;
   if (profiling_) ev_begin(&e0);
-  rc = launch_tc_heff(elem, split, tc_.d_tiles, (int)tc_.tiles.size(), tc_.d_outs, tc_.d_chunks, tc_.d_adds, tc_.max_kpad,
-                      tc_.max_npad, d_err_, stream_);
+  int rc = launch_tc_heff(elem, split, tc->d_tiles, (int)tc->tiles.size(), tc->d_outs, tc->d_chunks, tc->d_adds,
+                          tc->max_kpad, tc->max_npad, d_err_, stream_);
   if (rc) {
     err_ = "tensor-core H_eff: tile shape outside the supported range";
     return rc;
   }
-  if (profiling_) ev_end(e0, KC_TC_HEFF, tc_.flops_alg, tc_.flops_exec, tc_.bytes_alg);
+  if (profiling_) ev_end(e0, KC_TC_HEFF, tc->flops_alg, tc->flops_exec, tc->bytes_alg);
   return 0;
 }
 
@@ -1743,7 +1812,7 @@ int Engine::lanczos_run(int node, double tol, int max_krylov, bool mixed, int ma
       launch_dot(y_out_, y_out_, n, d_partial_, nrm2, stream_);
       launch_sqrt(nrm2, beta + j, stream_);
       k = j + 1;
-      launch_tridiag_lowest(alpha, beta, k, outv, svec, stream_);
+      launch_tridiag_lowest(alpha, beta, k, outv, svec, 0, stream_);
       cudaMemcpyAsync(host, outv, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream_);
       cudaMemcpyAsync(host + 2, beta + j, sizeof(double), cudaMemcpyDeviceToHost, stream_);
       if (!check(cudaStreamSynchronize(stream_), "lanczos")) return -3;
@@ -1755,6 +1824,7 @@ int Engine::lanczos_run(int node, double tol, int max_krylov, bool mixed, int ma
       if (j + 1 < kmax) launch_scale_inv_sqrt(y_out_, V_ + (j + 1) * ld, n, nrm2, stream_);
     }
     // Ritz vector x = V s
+    launch_tridiag_lowest(alpha, beta, k, outv, svec, 1, stream_);
     launch_combine(V_, ld, k, svec, xvec, n, stream_);
     if (done) break;
     // a low-precision operator stops improving at its rounding level: two
@@ -1769,10 +1839,13 @@ int Engine::lanczos_run(int node, double tol, int max_krylov, bool mixed, int ma
   // normalise
   launch_dot(xvec, xvec, n, d_partial_, nrm2, stream_);
   launch_scale_inv_sqrt(xvec, T_[node], n, nrm2, stream_);
-  *energy = theta;
-  *resid = res;
+  double fin[2] = {theta, res};
+  cudaMemcpyAsync(fin, outv, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream_);
+  if (!check(cudaStreamSynchronize(stream_), "lanczos end")) return -3;
+  *energy = fin[0];
+  *resid = fin[1];
   *iters = total_iters;
-  return check(cudaStreamSynchronize(stream_), "lanczos end") ? 0 : -3;
+  return 0;
 }
 
 // Node update.  FP64 path: Lanczos to tol.  Mixed path (bottom nodes):
@@ -1843,7 +1916,6 @@ int Engine::energy(double* total, double parts[N_CLASSES]) {
   if (!check(cudaStreamSynchronize(stream_), "energy")) return -3;
   *total = host[1] / host[0];
   for (int c = 0; c < N_CLASSES; ++c) parts[c] = host[2 + c] / host[0];
-  plan_node_ = -1;
   return 0;
 }
 
@@ -1908,7 +1980,6 @@ int Engine::node_import(int node, const std::vector<double>& host) {
   for (double v : host)
     if (!std::isfinite(v)) return -5;
   cudaMemcpyAsync(T_[node], host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, stream_);
-  plan_node_ = -1;
   return check(cudaStreamSynchronize(stream_), "import") ? 0 : -3;
 }
 
@@ -1918,8 +1989,7 @@ int Engine::load_tensors(const double* const* host, const long long* sizes, int 
     if (sizes[i] != layout_[i].size || !host[i]) return -1;
   for (int i = 0; i < n; ++i)
     cudaMemcpyAsync(T_[i], host[i], sizes[i] * sizeof(double), cudaMemcpyHostToDevice, stream_);
-  plan_node_ = -1;
-  tc_node_ = -1;
+  tc_w_node_ = -1;
   for (const TreeNode& nd : nodes_)
     if (nd.parent >= 0) {
       int rc = compute_up(nd.index);

@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <functional>
 #include <map>
 #include <memory>
 #include <string>
@@ -69,6 +70,7 @@ struct KPlan {
   void finalize(long long k_part);
   void upload(cudaStream_t s);
   void release();
+  ~KPlan() { release(); }
 };
 
 // A dense renormalized operator on a bond: O[i', i] (row-major dim x dim)
@@ -124,11 +126,13 @@ struct TcPlan {
   long long x_max_elems = 0, w_max_elems = 0;
   int max_kpad = 16, max_npad = 16;
   double flops_alg = 0, flops_exec = 0, bytes_alg = 0;
+  long long wtot = 0;            // elements of the W buffer this plan uses
   void clear() {
     tiles.clear(); outs.clear(); chunks.clear(); adds.clear(); xjobs.clear(); wjobs.clear();
-    x_max_elems = w_max_elems = 0; max_kpad = max_npad = 16; flops_alg = flops_exec = bytes_alg = 0;
+    x_max_elems = w_max_elems = wtot = 0; max_kpad = max_npad = 16; flops_alg = flops_exec = bytes_alg = 0;
   }
   void release();
+  ~TcPlan() { release(); }
 };
 
 // Per kernel-class timing of launches on the engine stream (CUDA events).
@@ -209,11 +213,7 @@ class Engine {
   int kernel_timing(KernelTiming out[KC_COUNT]);
   void reset_timing();
   int precision() const { return precision_; }
-  void set_precision(int p) {
-    precision_ = p;
-    tc_node_ = -1;
-    mixed_tol = p == PREC_TF32X3 ? 1e-7 : (p == PREC_TF32 ? 1e-5 : 1e-4);
-  }
+  void set_precision(int p);
   // mixed path tuning: residual target of the low-precision phase
   double mixed_tol = 0.0;
 
@@ -239,11 +239,6 @@ class Engine {
   std::map<long long, SiteOp*> site_ops_;   // packed (parity, kind, a, b)
   // row maps of bottom nodes: (node, term) -> per output c-sector
   std::map<std::pair<int, int>, std::vector<RowMap>> rowmaps_;
-  // H_eff plan cache for the current centre
-  int plan_node_ = -1;
-  int plan_cls_ = -2;
-  KPlan heff_stage_[3];
-  long long heff_z_elems_ = 0;
   double* zpool_ = nullptr;
   long long zpool_elems_ = 0;
   double* x_in_ = nullptr;
@@ -252,9 +247,44 @@ class Engine {
   double* scratch_ = nullptr;
   long long scratch_elems_ = 0;
   KPlan work_;
-  // mixed-precision state
-  TcPlan tc_;
-  int tc_node_ = -1;
+  // Plans are built once per (kind, node, ...) and replayed: their device
+  // pointers (tensors, bond operators, fixed buffers, Z pool) are stable
+  // until the Z pool or the staging buffers are reallocated, which clears
+  // the caches.  Split-K scratch is passed at launch, not stored.
+  std::map<std::tuple<int, int, int, int>, std::unique_ptr<KPlan>> plan_cache_;
+  KPlan* cached_plan(int kind, int a, int b, int c, const std::function<void(KPlan&)>& build);
+  int launch_plan(KPlan* pl, int fp32 = 0);
+  void clear_plan_caches();
+  // three-stage plans (Z stages of upper nodes, then the output stage)
+  void cached_plans(int kind, int a, int b, int n, KPlan** out, const std::function<void(KPlan**)>& build);
+  struct HeffPlans {
+    KPlan st[3];
+    long long z_elems = 0;       // Z pool prefix the stages use
+    long long scratch_need = 0;  // split-K scratch
+    double flops = 0.0;          // algorithmic flops of one product
+  };
+  std::map<std::pair<int, int>, std::unique_ptr<HeffPlans>> heff_cache_;
+  HeffPlans* heff_plans(int node, int cls_filter);
+  // persistent QR / move buffers (largest bond dimension squared)
+  double* qr_G_ = nullptr;
+  double* qr_Rinv_ = nullptr;
+  double* qr_Racc_ = nullptr;
+  double* qr_Rtmp_ = nullptr;
+  double* move_R_ = nullptr;
+  struct QrDesc {
+    long long* off = nullptr;
+    int* n = nullptr;
+    int* ld = nullptr;
+    int* status = nullptr;
+    int count = 0;
+    int max_n = 0;
+  };
+  std::map<std::pair<int, int>, QrDesc> qr_desc_;
+  // mixed-precision state: per-node plans; the staging buffers are shared
+  // and the environment blocks are re-staged when the centre changes
+  std::map<int, std::unique_ptr<TcPlan>> tc_cache_;
+  int tc_w_node_ = -1;          // node whose environment blocks are staged
+  void clear_tc_cache();
   void* xstage_ = nullptr;      // BF16 or FP32 padded staging of x
   float* xstage32_ = nullptr;   // FP32 padded staging (BF16 path)
   long long xstage_elems_ = 0;
@@ -269,7 +299,7 @@ class Engine {
   cudaEvent_t ev_get();
   void ev_begin(cudaEvent_t* e);
   void ev_end(cudaEvent_t a, int cls, double fa, double fe, double ba);
-  int build_tc_plan(int node);
+  TcPlan* tc_plan(int node);
   int apply_heff_mixed();
   bool mixed_node(int node) const;
   // Lanczos workspace
@@ -306,7 +336,6 @@ class Engine {
   RowMap build_rowmap_sector(int node, const SiteOp* A, const SiteOp* B, int out_sector, const std::vector<double>* vals);
   const std::vector<RowMap>& site_ham_map(int node, int leg, int cls);
   void build_heff_terms(int node, int cls_filter, std::vector<HTerm>* out);
-  int build_heff_plan(int node, int cls_filter);
   int run_plan(KPlan& pl);
   void plan_leg_apply(KPlan& pl, const Layout& LX, const double* X, const Layout& LY, double* Y, int leg,
                       const double* P, int dimP, int shiftP, bool transposed, double alpha);

@@ -95,10 +95,11 @@ void launch_cholesky_inv(double* G, double* Rinv, const long long* off, const in
 void launch_cgs2_qr(double* X, const long long* xoff, const int* rows, const int* cols, int count, double* R,
                     const long long* roff, int ldr, double dep_tol, double accept, cudaStream_t s);
 
-// Lowest eigenpair of the symmetric tridiagonal (alpha[0..k), beta[0..k-1)).
-// out[0] = theta, out[1] = |beta_k * s_k| (residual estimate), s[0..k) the
-// eigenvector with s[0] >= 0.  beta[k-1] is the trailing coupling.
-void launch_tridiag_lowest(const double* alpha, const double* beta, int k, double* out, double* svec,
+// Lowest eigenvalue of the symmetric tridiagonal (alpha[0..k), beta[0..k-1))
+// (1 <= k <= 128).  out[0] = theta, out[1] = |beta[k-1] * s_k| (Ritz residual
+// estimate; beta[k-1] is the trailing coupling).  With want_vec, s[0..k) gets
+// the unit eigenvector (s[0] >= 0) and out[0] its Rayleigh quotient.
+void launch_tridiag_lowest(const double* alpha, const double* beta, int k, double* out, double* svec, int want_vec,
                            cudaStream_t s);
 
 }  // namespace qed

@@ -3,6 +3,7 @@
 // GB300's FP64 rate is a small fraction of its tensor throughput, so these
 // kernels are simple register-tiled DFMA loops; the mixed-precision path
 // replaces the hot contraction with tensor-core kernels.
+#include <cfloat>
 #include <atomic>
 #include <cstdio>
 
@@ -403,75 +404,168 @@ __global__ void __launch_bounds__(QR_THREADS) cgs2_qr_kernel(double* X, const lo
   }
 }
 
-// Sturm-sequence count of eigenvalues below x for the tridiagonal.
-__device__ int sturm_count(const double* a, const double* b, int k, double x) {
-  int cnt = 0;
-  double d = 1.0;
-  for (int i = 0; i < k; ++i) {
-    double bb = i > 0 ? b[i - 1] * b[i - 1] : 0.0;
-    d = (a[i] - x) - (i > 0 ? bb / d : 0.0);
-    if (d == 0.0) d = -1e-300;
-    if (d < 0.0) ++cnt;
+// ------------------------------------------------------------ tridiagonal
+// Lowest eigenpair of the k x k symmetric tridiagonal T (diagonal a, squared
+// off-diagonal b2) of a Lanczos cycle.  The leading principal minors
+// p_i(x) = det(T_i - x I) obey p_i = (a_i - x) p_{i-1} - b2_{i-1} p_{i-2};
+// the number of sign changes along p_0 = 1, p_1, .., p_k is the number of
+// eigenvalues below x (Sturm).  Every operation is a multiply-add, so a warp
+// evaluates 32 counts at once; the state is rescaled by exact powers of two.
+constexpr int TRI_MAX = 128;
+
+__device__ __forceinline__ int dexp(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
+
+// exact rescaling of the recurrence state (p, pm[, d, dm]) by 2^-512 / 2^512
+__device__ __forceinline__ void rescale2(double& p, double& pm) {
+  const int e = dexp(p);
+  if (e > 1023 + 512) {
+    p *= 0x1p-512; pm *= 0x1p-512;
+  } else if (e < 1023 - 512 && dexp(pm) < 1023 - 512) {
+    p *= 0x1p+512; pm *= 0x1p+512;
+  }
+}
+
+__device__ int sturm_minors(const double* a, const double* b2, int k, double x) {
+  double pm = 1.0, p = a[0] - x;
+  int neg = __double2hiint(p) < 0 && p != 0.0;
+  int cnt = neg;
+  for (int i = 1; i < k; ++i) {
+    const double pn = fma(a[i] - x, p, -b2[i - 1] * pm);
+    const int nn = __double2hiint(pn) < 0 && pn != 0.0;   // zero counts as positive
+    cnt += nn ^ neg;
+    neg = nn;
+    pm = p;
+    p = pn;
+    rescale2(p, pm);
   }
   return cnt;
 }
 
-// Lowest eigenpair by bisection (Sturm counts) and two steps of inverse
-// iteration with a tridiagonal LU (Thomas algorithm).  Single thread.
-__global__ void tridiag_lowest_kernel(const double* alpha, const double* beta, int k, double* out, double* s) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double lo = 1e300, hi = -1e300;
-  for (int i = 0; i < k; ++i) {
-    double r = (i > 0 ? fabs(beta[i - 1]) : 0.0) + (i < k - 1 ? fabs(beta[i]) : 0.0);
-    lo = fmin(lo, alpha[i] - r);
-    hi = fmax(hi, alpha[i] + r);
+// -p_{k-1}(x) / p_k'(x): the squared last component of the unit eigenvector
+// of an eigenvalue x (ratio of the minor below to the derivative).
+__device__ double last_component_sq(const double* a, const double* b2, int k, double x) {
+  if (k == 1) return 1.0;
+  double pm = 1.0, p = a[0] - x, dm = 0.0, d = -1.0;
+  for (int i = 1; i < k; ++i) {
+    const double t = a[i] - x;
+    const double pn = fma(t, p, -b2[i - 1] * pm);
+    const double dn = fma(t, d, -fma(b2[i - 1], dm, p));
+    pm = p; p = pn; dm = d; d = dn;
+    const int e = dexp(p) > dexp(d) ? dexp(p) : dexp(d);
+    if (e > 1023 + 512) {
+      p *= 0x1p-512; pm *= 0x1p-512; d *= 0x1p-512; dm *= 0x1p-512;
+    } else if (e < 1023 - 512 && dexp(pm) < 1023 - 512 && dexp(dm) < 1023 - 512) {
+      p *= 0x1p+512; pm *= 0x1p+512; d *= 0x1p+512; dm *= 0x1p+512;
+    }
   }
-  double span = hi - lo;
-  lo -= 1e-12 * fabs(span) + 1e-300;
-  hi += 1e-12 * fabs(span) + 1e-300;
-  for (int it = 0; it < 200; ++it) {
-    double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
-    if (sturm_count(alpha, beta, k, mid) >= 1) hi = mid;
-    else lo = mid;
-  }
-  const double theta = 0.5 * (lo + hi);
-  // inverse iteration on (T - shift I) with shift slightly below theta
-  double scale = fmax(fabs(lo), fabs(hi));
-  double shift = theta - 1e-13 * fmax(scale, 1e-300) - 1e-300;
-  double x[128], cp[128], dp[128];
+  const double r = d != 0.0 ? -pm / d : 1.0;
+  return fmin(fmax(r, 0.0), 1.0);
+}
+
+// Eigenvector of T for the eigenvalue theta: inverse iteration with a shift
+// just below theta, tridiagonal LU (Thomas).  x normalised, x[0] >= 0.
+__device__ void inverse_iteration(const double* a, const double* b, int k, double theta, double scale, int iters,
+                                  double* x) {
+  double cp[TRI_MAX], dp[TRI_MAX];
+  const double shift = theta - 1e-13 * fmax(scale, 1e-300) - 1e-300;
   for (int i = 0; i < k; ++i) x[i] = 1.0;
-  for (int iter = 0; iter < 3; ++iter) {
-    // Thomas: sub = beta[i-1], diag = alpha[i]-shift, sup = beta[i]
-    double denom = alpha[0] - shift;
+  for (int it = 0; it < iters; ++it) {
+    double denom = a[0] - shift;
     if (denom == 0.0) denom = 1e-300;
-    cp[0] = (k > 1 ? beta[0] : 0.0) / denom;
+    cp[0] = (k > 1 ? b[0] : 0.0) / denom;
     dp[0] = x[0] / denom;
     for (int i = 1; i < k; ++i) {
-      double m = (alpha[i] - shift) - beta[i - 1] * cp[i - 1];
+      double m = (a[i] - shift) - b[i - 1] * cp[i - 1];
       if (m == 0.0) m = 1e-300;
-      cp[i] = (i < k - 1 ? beta[i] : 0.0) / m;
-      dp[i] = (x[i] - beta[i - 1] * dp[i - 1]) / m;
+      const double inv = 1.0 / m;
+      cp[i] = (i < k - 1 ? b[i] : 0.0) * inv;
+      dp[i] = (x[i] - b[i - 1] * dp[i - 1]) * inv;
     }
     x[k - 1] = dp[k - 1];
     for (int i = k - 2; i >= 0; --i) x[i] = dp[i] - cp[i] * x[i + 1];
     double nrm = 0.0;
     for (int i = 0; i < k; ++i) nrm += x[i] * x[i];
-    nrm = sqrt(nrm);
-    for (int i = 0; i < k; ++i) x[i] /= nrm;
+    const double inv = 1.0 / sqrt(nrm);
+    for (int i = 0; i < k; ++i) x[i] *= inv;
   }
-  const double sgn = x[0] < 0.0 ? -1.0 : 1.0;
-  for (int i = 0; i < k; ++i) s[i] = sgn * x[i];
-  // Rayleigh quotient of the tridiagonal (more accurate than the bisection midpoint)
-  double rq = 0.0;
-  for (int i = 0; i < k; ++i) {
-    double v = alpha[i] * s[i];
-    if (i > 0) v += beta[i - 1] * s[i - 1];
-    if (i < k - 1) v += beta[i] * s[i + 1];
-    rq += s[i] * v;
+  if (x[0] < 0.0)
+    for (int i = 0; i < k; ++i) x[i] = -x[i];
+}
+
+// One warp.  Multisection: each round the 32 lanes count at 32 interior
+// points of [lo, hi] and the bracket shrinks 33-fold, until it is a few
+// ulps wide.  out[0] = theta, out[1] = |beta[k-1]| |s_k| (the Ritz residual
+// estimate).  With want_vec the eigenvector goes to s and out[0] is its
+// Rayleigh quotient; the vector is also formed when s_k is too small for
+// the minor ratio to resolve.
+__global__ void __launch_bounds__(32) tridiag_lowest_kernel(const double* __restrict__ alpha,
+                                                            const double* __restrict__ beta, int k, double* out,
+                                                            double* s, int want_vec) {
+  __shared__ double a[TRI_MAX], b[TRI_MAX], b2[TRI_MAX];
+  const int lane = threadIdx.x;
+  for (int i = lane; i < k; i += 32) {
+    a[i] = alpha[i];
+    const double bi = i < k - 1 ? beta[i] : 0.0;
+    b[i] = bi;
+    b2[i] = bi * bi;
   }
-  out[0] = rq;
-  out[1] = fabs(beta[k - 1] * s[k - 1]);
+  __syncwarp();
+  // Gershgorin bracket
+  double lo = 1e300, hi = -1e300;
+  for (int i = lane; i < k; i += 32) {
+    const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + fabs(b[i]);
+    lo = fmin(lo, a[i] - r);
+    hi = fmax(hi, a[i] + r);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  const double span = hi - lo;
+  const double scale = fmax(fabs(lo), fabs(hi));
+  lo -= 1e-12 * span + 1e-300;
+  hi += 1e-12 * span + 1e-300;
+  for (int round = 0; round < 64; ++round) {
+    const double w = hi - lo;
+    if (w <= 4.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 1e-300) break;
+    const double x = lo + w * ((double)(lane + 1) * (1.0 / 33.0));
+    const unsigned above = __ballot_sync(0xffffffffu, sturm_minors(a, b2, k, x) >= 1);
+    double nlo, nhi;
+    if (above == 0u) {
+      nlo = __shfl_sync(0xffffffffu, x, 31);
+      nhi = hi;
+    } else {
+      const int f = __ffs(above) - 1;
+      nhi = __shfl_sync(0xffffffffu, x, f);
+      const double xl = __shfl_sync(0xffffffffu, x, f > 0 ? f - 1 : 0);
+      nlo = f > 0 ? xl : lo;
+    }
+    if (!(nhi - nlo < w)) break;   // no progress left at this precision
+    lo = nlo;
+    hi = nhi;
+  }
+  if (lane != 0) return;
+  const double theta = 0.5 * (lo + hi);
+  double sk = sqrt(last_component_sq(a, b2, k, theta));
+  double th = theta;
+  if (want_vec || sk < 1e-4) {
+    double x[TRI_MAX];
+    inverse_iteration(a, b, k, theta, scale, want_vec ? 3 : 2, x);
+    sk = fabs(x[k - 1]);
+    if (want_vec) {
+      double rq = 0.0;
+      for (int i = 0; i < k; ++i) {
+        double v = a[i] * x[i];
+        if (i > 0) v += b[i - 1] * x[i - 1];
+        if (i < k - 1) v += b[i] * x[i + 1];
+        rq += x[i] * v;
+      }
+      th = rq;
+      for (int i = 0; i < k; ++i) s[i] = x[i];
+    }
+  }
+  out[0] = th;
+  out[1] = fabs(beta[k - 1]) * sk;
 }
 
 int grid_for(long long n) {
@@ -599,9 +693,10 @@ void launch_cgs2_qr(double* X, const long long* xoff, const int* rows, const int
   count_launches(1);
 }
 
-void launch_tridiag_lowest(const double* alpha, const double* beta, int k, double* out, double* s,
+void launch_tridiag_lowest(const double* alpha, const double* beta, int k, double* out, double* s, int want_vec,
                            cudaStream_t st) {
-  tridiag_lowest_kernel<<<1, 32, 0, st>>>(alpha, beta, k, out, s);
+  if (k <= 0 || k > TRI_MAX) return;
+  tridiag_lowest_kernel<<<1, 32, 0, st>>>(alpha, beta, k, out, s, want_vec);
   count_launches(1);
 }
 

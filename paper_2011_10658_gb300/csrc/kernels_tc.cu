@@ -17,6 +17,7 @@
 // shared-memory stages so the gather of term j+1 overlaps the MMAs of term
 // j.  Every mbarrier wait is bounded; a timeout sets *err and the CTA
 // drains, frees its TMEM and returns.
+#include <algorithm>
 #include <cuda_bf16.h>
 
 #include <cstdio>
@@ -228,32 +229,33 @@ __global__ void __launch_bounds__(TC_THREADS) tc_heff_kernel(const TcTile* __res
 
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
+// One warp per padded row, lanes along the row: coalesced reads of the
+// FP64 source and writes of the staged operand (no index division).
 template <int ELEM, int MODE>
-__global__ void convert_kernel(const ConvJob* __restrict__ jobs) {
+__global__ void __launch_bounds__(256) convert_kernel(const ConvJob* __restrict__ jobs) {
   const ConvJob j = jobs[blockIdx.y];
-  const long long total = (long long)j.rows * j.kpad;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int r = (int)(e / j.kpad), c = (int)(e - (long long)r * j.kpad);
-    const double v = c < j.cols ? j.scale * j.src[(long long)r * j.ld_src + (long long)c * j.cs_src] : 0.0;
-    if (MODE == 0) {
-      if (ELEM == 2)
-        ((__nv_bfloat16*)j.dst)[e] = __double2bfloat16(v);
-      else
-        ((float*)j.dst)[e] = (float)v;
-    } else {
-      const float hi = tf32_hi((float)v);
-      const float lo = (float)(v - (double)hi);
-      float* d = (float*)j.dst;
-      if (MODE == 1) {
-        d[(long long)r * 2 * j.kpad + c] = hi;
-        d[(long long)r * 2 * j.kpad + j.kpad + c] = lo;
+  const int lane = threadIdx.x & 31;
+  const int warps = (int)(gridDim.x * (blockDim.x >> 5));
+  for (int r = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)); r < j.rows; r += warps) {
+    const double* src = j.src + (long long)r * j.ld_src;
+    for (int c = lane; c < j.kpad; c += 32) {
+      const double v = c < j.cols ? j.scale * src[(long long)c * j.cs_src] : 0.0;
+      const long long e = (long long)r * j.kpad + c;
+      if (MODE == 0) {
+        if (ELEM == 2)
+          ((__nv_bfloat16*)j.dst)[e] = __double2bfloat16(v);
+        else
+          ((float*)j.dst)[e] = (float)v;
       } else {
-        d[(long long)r * 2 * j.kpad + c] = hi;
-        d[(long long)r * 2 * j.kpad + j.kpad + c] = lo;
+        // [hi | lo] rows: hi = TF32-truncated, lo = FP32 residual
+        const float hi = tf32_hi((float)v);
+        const float lo = (float)(v - (double)hi);
+        float* d = (float*)j.dst + (long long)r * 2 * j.kpad;
+        d[c] = hi;
+        d[j.kpad + c] = lo;
       }
+      if (j.dst32) j.dst32[e] = (float)v;
     }
-    if (j.dst32) j.dst32[e] = (float)v;
   }
 }
 
@@ -285,8 +287,10 @@ int launch_tc_heff(int elem, int split, const TcTile* tiles, int n_tiles, const 
 
 void launch_convert(int elem, int mode, const ConvJob* jobs, int n_jobs, long long max_elems, cudaStream_t s) {
   if (n_jobs <= 0) return;
-  long long gx = (max_elems + 255) / 256;
-  if (gx > 64) gx = 64;
+  // rows <= max_elems / 16 (kpad >= 16); 8 rows per block, about 4 blocks per SM in total
+  long long gx = (max_elems / 16 + 7) / 8;
+  const long long cap = std::max(1LL, 608LL / n_jobs);
+  if (gx > cap) gx = cap;
   if (gx < 1) gx = 1;
   dim3 grid((unsigned)gx, (unsigned)n_jobs);
   if (mode == 1)
