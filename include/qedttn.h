@@ -111,6 +111,13 @@ int qed_model_terms(const qed_model *m, double *coef, int32_t *cls, int32_t *n_o
 /* Tree: per node (layer, axis, child_kind0, child0, child_kind1, child1,
  * parent); child_kind 0 = site, 1 = node; parent -1 for the root. */
 int qed_model_tree(const qed_model *m, int32_t *nodes /* [n][7] */, int64_t cap, int64_t *n);
+/* Order of the node updates in one sweep (Methods: the sweep runs from the
+ * lowest to the highest layer; the order inside a layer is not given there).
+ * Inside a layer: depth-first order of the tree, first child first, the
+ * direction alternating between consecutive layers.  order[i] = node id;
+ * *n = number of nodes.  Caller-owned buffer of cap entries (QED_EINVAL if
+ * too small; a NULL buffer only reports *n). */
+int qed_model_sweep_order(const qed_model *m, int32_t *order, int64_t cap, int64_t *n);
 /* Bond sector table for bond dimension chi: for the bond above each node,
  * its sectors as consecutive (node, q, dim) triples. */
 int qed_model_sectors(const qed_model *m, int32_t chi, int32_t *triples, int64_t cap, int64_t *n);
@@ -132,8 +139,8 @@ typedef struct {
   double seconds;           /* wall time of the call */
 } ttn_sweep_stats;
 
-/* n_sweeps full sweeps: nodes in number order (layer by layer from the
- * bottom), the centre moved along the tree with per-sector QR, each node
+/* n_sweeps full sweeps: nodes in qed_model_sweep_order (layer by layer from
+ * the bottom), the centre moved along the tree with per-sector QR, each node
  * replaced by the lowest eigenvector of its H_eff (Lanczos with full
  * reorthogonalisation, started from the current tensor, stopping at
  * residual <= tol |theta|, restarted every max_krylov steps).

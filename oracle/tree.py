@@ -139,6 +139,30 @@ def allocate(chi, w, cap, n, N, Q):
     return {q: c for q, c in out.items() if c > 0}
 
 
+def sweep_order(nodes):
+    """Order of the node updates within one sweep.  The Methods section runs
+    each sweep from the lowest to the highest layer and fixes no order
+    inside a layer.  Reading taken here: inside a layer the nodes follow a
+    depth-first walk of the tree (first child before second child), and the
+    direction alternates from one layer to the next, so that consecutive
+    updates sit few bonds apart and each layer starts next to where the
+    previous one ended."""
+    root = len(nodes) - 1
+    rank = {}
+    stack = [root]
+    while stack:
+        i = stack.pop()
+        rank[i] = len(rank)
+        kids = [c for (kind, c) in nodes[i].children if kind == "node"]
+        stack.extend(reversed(kids))
+    order = []
+    layers = sorted({nd.layer for nd in nodes})
+    for li, layer in enumerate(layers):
+        row = sorted((nd.index for nd in nodes if nd.layer == layer), key=rank.get)
+        order.extend(row if li % 2 == 0 else row[::-1])
+    return order
+
+
 def sector_table(p: _model.Params, chi, nodes=None):
     """Bond sectors {q: chi_q} for the bond above each node, bottom-up.
     The root's parent bond is {Q: 1}."""

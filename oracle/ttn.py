@@ -353,10 +353,10 @@ class TTN:
         return e
 
     def sweep(self, tol=1e-12):
-        """One sweep: nodes in number order (layer by layer from the bottom)."""
+        """One sweep: layer by layer from the bottom, in tree.sweep_order."""
         out = []
-        for nd in self.nodes:
-            out.append(self.optimize_node(nd.index, tol))
+        for i in _tree.sweep_order(self.nodes):
+            out.append(self.optimize_node(i, tol))
         return out
 
     # ------------------------------------------------------------ measurement

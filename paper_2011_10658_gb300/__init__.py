@@ -89,6 +89,14 @@ class Model:
         check(lib().qed_model_tree(self._h, _ptr(out, ctypes.c_int32), n.value, ctypes.byref(n)))
         return out
 
+    def sweep_order(self):
+        """Node ids in the order one sweep updates them."""
+        n = ctypes.c_int64()
+        check(lib().qed_model_sweep_order(self._h, None, 0, ctypes.byref(n)))
+        out = np.zeros(n.value, dtype=np.int32)
+        check(lib().qed_model_sweep_order(self._h, _ptr(out, ctypes.c_int32), n.value, ctypes.byref(n)))
+        return out
+
     def sectors(self, chi):
         """List over nodes of {q: dim} for the bond above each node."""
         n = ctypes.c_int64()

@@ -43,6 +43,7 @@ SIGNATURES = [
     ("qed_model_info", c_int, [c_void_p, c_int32_p, c_int32_p, c_int32_p, c_double_p]),
     ("qed_model_terms", c_int, [c_void_p, c_double_p, c_int32_p, c_int32_p, c_int32_p, c_int64, c_int64_p]),
     ("qed_model_tree", c_int, [c_void_p, c_int32_p, c_int64, c_int64_p]),
+    ("qed_model_sweep_order", c_int, [c_void_p, c_int32_p, c_int64, c_int64_p]),
     ("qed_model_sectors", c_int, [c_void_p, c_int32, c_int32_p, c_int64, c_int64_p]),
     ("ttn_create", c_int, [c_void_p, c_int32, ctypes.c_uint64, c_int, c_void_p, ctypes.POINTER(c_void_p)]),
     ("ttn_destroy", None, [c_void_p]),

@@ -151,6 +151,16 @@ QED_API int qed_model_tree(const qed_model* m, int32_t* nodes, int64_t cap, int6
   return QED_OK;
 }
 
+QED_API int qed_model_sweep_order(const qed_model* m, int32_t* order, int64_t cap, int64_t* n) {
+  if (!m) return fail(QED_EINVAL, "null model");
+  const std::vector<int> o = qed::sweep_order(m->nodes);
+  if (n) *n = (int64_t)o.size();
+  if (!order || cap <= 0) return QED_OK;
+  if (cap < (int64_t)o.size()) return fail(QED_EINVAL, "buffer too small");
+  for (size_t i = 0; i < o.size(); ++i) order[i] = o[i];
+  return QED_OK;
+}
+
 QED_API int qed_model_sectors(const qed_model* m, int32_t chi, int32_t* triples, int64_t cap, int64_t* n) {
   if (!m) return fail(QED_EINVAL, "null model");
   if (chi < 1 || chi > 4096) return fail(QED_EINVAL, "chi out of range");

@@ -22,6 +22,8 @@ namespace qed {
 namespace {
 constexpr long long kKPart = 4096;     // split-K granularity for tall contractions
 constexpr int kMaxKrylov = 128;
+constexpr double kReorthRatio = 0.5;
+constexpr int kThickKeep = 8;          // Ritz vectors kept by a thick restart   // second Gram-Schmidt pass if ||w||^2 dropped below half
 // Centre-move QR rank handling: a sector whose QR diagonal falls below
 // kQrFallback x (largest column norm) is factorised by Gram-Schmidt, where a
 // remainder below kQrDependent x (largest column norm) marks a dependent
@@ -117,12 +119,21 @@ void KPlan::finalize(long long k_part) {
   tiles.clear();
   red.clear();
   scratch_need = 0;
+  // K per part: small enough that the launch has about four tiles per SM
+  // when the plan has few, long contractions (a Gram matrix), at most k_part
+  long long work = 0;
+  for (const KOutput& o : outs) {
+    long long ktot = 0;
+    for (int c = o.chunk_begin; c < o.chunk_end; ++c) ktot += chunks[c].add ? 1 : chunks[c].K;
+    work += (long long)((o.M + KT_BM - 1) / KT_BM) * ((o.N + KT_BN - 1) / KT_BN) * ktot;
+  }
+  k_part = std::max(256LL, std::min(k_part, work / (4 * 152)));
   for (size_t oi = 0; oi < outs.size(); ++oi) {
     KOutput& o = outs[oi];
     const int tm = (o.M + KT_BM - 1) / KT_BM, tn = (o.N + KT_BN - 1) / KT_BN;
     long long ktot = 0;
     for (int c = o.chunk_begin; c < o.chunk_end; ++c) ktot += chunks[c].add ? 1 : chunks[c].K;
-    const bool split = ktot > 2 * k_part && tm * tn <= 8;
+    const bool split = ktot > 2 * k_part && tm * tn <= 16;
     std::vector<std::pair<int, int>> parts;   // ranges in nc
     const int begin = (int)nc.size();
     if (!split) {
@@ -466,7 +477,7 @@ Engine::Engine(const Params& p, int chi, uint64_t seed, int precision, cudaStrea
   tmp_ = (double*)dalloc(nmax_ * sizeof(double));
   d_scal_ = (double*)dalloc(8192 * sizeof(double));
   d_partial_ = (double*)dalloc(304 * (kMaxKrylov + 2) * sizeof(double));
-  d_err_ = (int*)dalloc(sizeof(int));
+  d_err_ = (int*)dalloc(4 * sizeof(int));   // [0] tensor-core wait flag, [1] thick-restart count
   cudaMemsetAsync(d_err_, 0, sizeof(int), stream_);
   long long dmax = 1;
   for (const Sectors& b : bonds_) dmax = std::max<long long>(dmax, b.total());
@@ -500,6 +511,7 @@ Engine::~Engine() {
   if (scratch_) cudaFree(scratch_);
   if (zpool_) cudaFree(zpool_);
   if (V_) cudaFree(V_);
+  if (zb_) cudaFree(zb_);
   for (void* p : allocs_) cudaFree(p);
 }
 
@@ -1785,19 +1797,54 @@ int Engine::lanczos_run(int node, double tol, int max_krylov, bool mixed, int ma
   double* outv = d_scal_ + 384;
   double* coef = d_scal_ + 512;
   double* nrm2 = d_scal_ + 640;
+  double* nrm_pre = d_scal_ + 641;
+  double* nrm_mid = d_scal_ + 642;
   double* xvec = tmp_;
   const long long ld = nmax_;
+  const int keep = std::min(kThickKeep, kmax / 4);
+  if (keep >= 1 && zb_elems_ < (long long)keep * nmax_) {
+    if (zb_) { untrack(zb_); cudaFree(zb_); }
+    zb_elems_ = (long long)keep * nmax_;
+    if (!check(cudaMalloc(&zb_, zb_elems_ * sizeof(double)), "restart basis")) return -2;
+    track(zb_, zb_elems_ * sizeof(double));
+  }
+  double* Cmat = d_scal_ + 1024;   // k x keep combination of a thick restart
   launch_copy(T_[node], xvec, n, stream_);
+  launch_dot(xvec, xvec, n, d_partial_, nrm2, stream_);
+  launch_scale_inv_sqrt(xvec, V_, n, nrm2, stream_);
   int total_iters = 0;
   double theta = 0.0, res = 0.0, prev_res = 1e300;
   int stalls = 0;
+  int j0 = 0;   // vectors carried into the cycle (thick restart)
+  int k = 0;
   for (int restart = 0; restart < max_restarts; ++restart) {
-    launch_dot(xvec, xvec, n, d_partial_, nrm2, stream_);
-    launch_scale_inv_sqrt(xvec, V_, n, nrm2, stream_);
-    int k = 0;
+    if (restart > 0) {
+      // thick restart: keep the lowest Ritz vectors, continue from the
+      // residual vector stored in column kmax
+      if (keep < 1) {
+        launch_tridiag_lowest(alpha, beta, k, outv, svec, 1, stream_);
+        launch_combine(V_, ld, k, svec, xvec, n, stream_);
+        launch_dot(xvec, xvec, n, d_partial_, nrm2, stream_);
+        launch_scale_inv_sqrt(xvec, V_, n, nrm2, stream_);
+        j0 = 0;
+      } else {
+        launch_lanczos_restart(alpha, beta, k, keep, Cmat, d_err_ + 1, stream_);
+        int p = 0;
+        cudaMemcpyAsync(&p, d_err_ + 1, sizeof(int), cudaMemcpyDeviceToHost, stream_);
+        if (!check(cudaStreamSynchronize(stream_), "thick restart")) return -3;
+        if (p < 1 || p > keep) {
+          err_ = "thick restart: invalid kept count";
+          return -3;
+        }
+        launch_rotate_basis(V_, ld, k, Cmat, p, zb_, n, stream_);
+        cudaMemcpyAsync(V_, zb_, (size_t)p * ld * sizeof(double), cudaMemcpyDeviceToDevice, stream_);
+        launch_copy(V_ + (long long)kmax * ld, V_ + (long long)p * ld, n, stream_);
+        j0 = p;
+      }
+    }
     bool done = false;
     double host[4] = {0, 0, 0, 0};
-    for (int j = 0; j < kmax; ++j) {
+    for (int j = j0; j < kmax; ++j) {
       double* vj = V_ + j * ld;
       int rc = apply_heff(vj, y_out_, -1);
       if (rc) return rc;
@@ -1805,10 +1852,14 @@ int Engine::lanczos_run(int node, double tol, int max_krylov, bool mixed, int ma
       launch_dot(vj, y_out_, n, d_partial_, alpha + j, stream_);
       launch_axpby(vj, y_out_, n, alpha + j, 0.0, -1.0, nullptr, 1.0, stream_);
       if (j > 0) launch_axpby(V_ + (j - 1) * ld, y_out_, n, beta + (j - 1), 0.0, -1.0, nullptr, 1.0, stream_);
-      for (int pass = 0; pass < 2; ++pass) {
-        launch_multidot(V_, ld, j + 1, y_out_, n, d_partial_, coef, stream_);
-        launch_multiaxpy(V_, ld, j + 1, coef, y_out_, n, stream_);
-      }
+      // full reorthogonalisation: one classical Gram-Schmidt pass, and a
+      // second one only if the first removed more than half of ||w||^2
+      launch_dot(y_out_, y_out_, n, d_partial_, nrm_pre, stream_);
+      launch_multidot(V_, ld, j + 1, y_out_, n, d_partial_, coef, stream_);
+      launch_multiaxpy(V_, ld, j + 1, coef, y_out_, n, stream_);
+      launch_dot(y_out_, y_out_, n, d_partial_, nrm_mid, stream_);
+      launch_multidot(V_, ld, j + 1, y_out_, n, d_partial_, coef, stream_, nrm_mid, nrm_pre, kReorthRatio);
+      launch_multiaxpy(V_, ld, j + 1, coef, y_out_, n, stream_, nrm_mid, nrm_pre, kReorthRatio);
       launch_dot(y_out_, y_out_, n, d_partial_, nrm2, stream_);
       launch_sqrt(nrm2, beta + j, stream_);
       k = j + 1;
@@ -1821,20 +1872,23 @@ int Engine::lanczos_run(int node, double tol, int max_krylov, bool mixed, int ma
       res = host[1];
       const bool breakdown = bj <= 1e-13 * std::max(1.0, std::fabs(theta));
       if (res <= tol * std::max(1e-300, std::fabs(theta)) || breakdown) { done = true; break; }
-      if (j + 1 < kmax) launch_scale_inv_sqrt(y_out_, V_ + (j + 1) * ld, n, nrm2, stream_);
+      // next Lanczos vector (column kmax holds the residual vector of a full cycle)
+      launch_scale_inv_sqrt(y_out_, V_ + (j + 1) * ld, n, nrm2, stream_);
     }
-    // Ritz vector x = V s
-    launch_tridiag_lowest(alpha, beta, k, outv, svec, 1, stream_);
-    launch_combine(V_, ld, k, svec, xvec, n, stream_);
     if (done) break;
     // a low-precision operator stops improving at its rounding level: two
-    // restart cycles without a 2 % gain end the low-precision phase
+    // restart cycles within 1000x of that level without a 2 % gain end the
+    // low-precision phase
     if (mixed) {
-      stalls = res > 0.98 * prev_res ? stalls + 1 : 0;
+      const bool near_floor = res <= 1e3 * mixed_tol * std::fabs(theta);
+      stalls = (near_floor && res > 0.98 * prev_res) ? stalls + 1 : 0;
       if (stalls >= 2) break;
     }
     prev_res = std::min(prev_res, res);
   }
+  // Ritz vector x = V s of the last cycle
+  launch_tridiag_lowest(alpha, beta, k, outv, svec, 1, stream_);
+  launch_combine(V_, ld, k, svec, xvec, n, stream_);
   use_mixed_ = false;
   // normalise
   launch_dot(xvec, xvec, n, d_partial_, nrm2, stream_);
@@ -1887,7 +1941,7 @@ int Engine::optimize_node(int node, double tol, int max_krylov, SweepStats* st, 
 }
 
 int Engine::sweep(double tol, int max_krylov, SweepStats* st, std::vector<double>* energies) {
-  for (int i = 0; i < (int)nodes_.size(); ++i) {
+  for (int i : sweep_order(nodes_)) {
     double e = 0;
     int rc = optimize_node(i, tol, max_krylov, st, &e);
     if (rc) return rc;

@@ -164,7 +164,7 @@ class Engine {
   Engine(const Params& p, int chi, uint64_t seed, int precision, cudaStream_t stream);
   ~Engine();
 
-  // One full sweep (nodes in number order); energies[i] per node update.
+  // One full sweep (nodes in sweep_order); energies[i] per node update.
   int sweep(double tol, int max_krylov, SweepStats* st, std::vector<double>* energies);
   // Energy with the current centre tensor; class-resolved parts.
   int energy(double* total, double parts[N_CLASSES]);
@@ -304,6 +304,8 @@ class Engine {
   bool mixed_node(int node) const;
   // Lanczos workspace
   double* V_ = nullptr;
+  double* zb_ = nullptr;        // rotated Ritz vectors of a thick restart
+  long long zb_elems_ = 0;
   int kmax_alloc_ = 0;
   double* d_scal_ = nullptr;   // alpha[128], beta[128], s[128], out[8], coeffs[128], partials
   double* d_partial_ = nullptr;

@@ -60,12 +60,16 @@ void launch_kc_reduce(const KOutput* outs, int n_outs, const int* red_list, int 
 // ---- vector kernels (FP64) ----
 // partial sums per block then a single-block finish: deterministic.
 void launch_dot(const double* x, const double* y, long long n, double* partial, double* out, cudaStream_t s);
-// out[j] = <Q_j, w> for j < k (Q columns of length n, stride ldq)
+// out[j] = <Q_j, w> for j < k (Q columns of length n, stride ldq).
+// Optional gate (device scalars): the call does nothing when
+// *gate_num >= ratio * *gate_den (a skipped reorthogonalisation pass).
 void launch_multidot(const double* Q, long long ldq, int k, const double* w, long long n, double* partial,
-                     double* out, cudaStream_t s);
-// w -= sum_j Q_j c[j]
+                     double* out, cudaStream_t s, const double* gate_num = nullptr, const double* gate_den = nullptr,
+                     double ratio = 0.0);
+// w -= sum_j Q_j c[j]  (same optional gate)
 void launch_multiaxpy(const double* Q, long long ldq, int k, const double* c, double* w, long long n,
-                      cudaStream_t s);
+                      cudaStream_t s, const double* gate_num = nullptr, const double* gate_den = nullptr,
+                      double ratio = 0.0);
 // x = sum_j c[j] Q_j
 void launch_combine(const double* Q, long long ldq, int k, const double* c, double* x, long long n, cudaStream_t s);
 // out[0] = sqrt(max(in[0], 0))
@@ -101,6 +105,14 @@ void launch_cgs2_qr(double* X, const long long* xoff, const int* rows, const int
 // the unit eigenvector (s[0] >= 0) and out[0] its Rayleigh quotient.
 void launch_tridiag_lowest(const double* alpha, const double* beta, int k, double* out, double* svec, int want_vec,
                            cudaStream_t s);
+// Thick restart (keep the m <= 8 lowest Ritz pairs of the k x k tridiagonal,
+// k <= 128): writes the k x p combination C (row-major), the new leading
+// p x p tridiagonal into alpha/beta with beta[p-1] the coupling to the
+// residual vector, and p (1 <= p <= m) to *p_out.
+void launch_lanczos_restart(double* alpha, double* beta, int k, int m, double* C, int* p_out, cudaStream_t s);
+// Z[:, i] = sum_r V[:, r] C[r * p + i], i < p <= 8 (columns of length n, stride ld).
+void launch_rotate_basis(const double* V, long long ld, int k, const double* C, int p, double* Z, long long n,
+                         cudaStream_t s);
 
 }  // namespace qed
 

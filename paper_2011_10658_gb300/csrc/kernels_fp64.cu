@@ -150,7 +150,16 @@ __global__ void dot_partial_kernel(const double* __restrict__ x, const double* _
   if (threadIdx.x == 0) partial[blockIdx.x] = v;
 }
 
-__global__ void finish_kernel(const double* __restrict__ partial, int count, int stride, double* __restrict__ out) {
+// Gate of a conditional reorthogonalisation pass (Daniel-Gragg-Kaufman-Stewart):
+// the pass runs only if ||w||^2 after the first pass fell below ratio times
+// ||w||^2 before it.
+__device__ __forceinline__ bool gated_off(const double* num, const double* den, double ratio) {
+  return num && *num >= ratio * *den;
+}
+
+__global__ void finish_kernel(const double* __restrict__ partial, int count, int stride, double* __restrict__ out,
+                              const double* gate_num = nullptr, const double* gate_den = nullptr, double ratio = 0.0) {
+  if (gated_off(gate_num, gate_den, ratio)) return;
   // blockIdx.x selects which vector of partials (multidot)
   double v = 0.0;
   for (int i = threadIdx.x; i < count; i += blockDim.x) v += partial[(long long)blockIdx.x * stride + i];
@@ -159,7 +168,9 @@ __global__ void finish_kernel(const double* __restrict__ partial, int count, int
 }
 
 __global__ void multidot_partial_kernel(const double* __restrict__ Q, long long ldq, int k,
-                                        const double* __restrict__ w, long long n, double* __restrict__ partial) {
+                                        const double* __restrict__ w, long long n, double* __restrict__ partial,
+                                        const double* gate_num, const double* gate_den, double ratio) {
+  if (gated_off(gate_num, gate_den, ratio)) return;
   // blockIdx.y = column j
   const int j = blockIdx.y;
   const double* q = Q + (long long)j * ldq;
@@ -171,7 +182,9 @@ __global__ void multidot_partial_kernel(const double* __restrict__ Q, long long 
 }
 
 __global__ void multiaxpy_kernel(const double* __restrict__ Q, long long ldq, int k, const double* __restrict__ c,
-                                 double* __restrict__ w, long long n) {
+                                 double* __restrict__ w, long long n, const double* gate_num, const double* gate_den,
+                                 double ratio) {
+  if (gated_off(gate_num, gate_den, ratio)) return;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     double v = w[i];
     for (int j = 0; j < k; ++j) v = fma(-c[j], Q[(long long)j * ldq + i], v);
@@ -412,6 +425,7 @@ __global__ void __launch_bounds__(QR_THREADS) cgs2_qr_kernel(double* X, const lo
 // eigenvalues below x (Sturm).  Every operation is a multiply-add, so a warp
 // evaluates 32 counts at once; the state is rescaled by exact powers of two.
 constexpr int TRI_MAX = 128;
+constexpr int RESTART_MAX = 8;   // Ritz vectors kept by a thick restart
 
 __device__ __forceinline__ int dexp(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
 
@@ -463,12 +477,14 @@ __device__ double last_component_sq(const double* a, const double* b2, int k, do
 }
 
 // Eigenvector of T for the eigenvalue theta: inverse iteration with a shift
-// just below theta, tridiagonal LU (Thomas).  x normalised, x[0] >= 0.
+// just below theta, tridiagonal LU (Thomas), orthogonalised against the
+// n_prev rows of prev (stride ld) (vectors of lower eigenvalues of a
+// cluster).  x normalised, x[0] >= 0 when n_prev == 0.
 __device__ void inverse_iteration(const double* a, const double* b, int k, double theta, double scale, int iters,
-                                  double* x) {
+                                  double* x, const double* prev, int ld, int n_prev) {
   double cp[TRI_MAX], dp[TRI_MAX];
   const double shift = theta - 1e-13 * fmax(scale, 1e-300) - 1e-300;
-  for (int i = 0; i < k; ++i) x[i] = 1.0;
+  for (int i = 0; i < k; ++i) x[i] = n_prev == 0 ? 1.0 : 1.0 + 0.37 * (double)(i % (n_prev + 2));
   for (int it = 0; it < iters; ++it) {
     double denom = a[0] - shift;
     if (denom == 0.0) denom = 1e-300;
@@ -483,53 +499,32 @@ __device__ void inverse_iteration(const double* a, const double* b, int k, doubl
     }
     x[k - 1] = dp[k - 1];
     for (int i = k - 2; i >= 0; --i) x[i] = dp[i] - cp[i] * x[i + 1];
+    for (int pass = 0; pass < 2; ++pass)
+      for (int q = 0; q < n_prev; ++q) {
+        double h = 0.0;
+        for (int i = 0; i < k; ++i) h += prev[q * ld + i] * x[i];
+        for (int i = 0; i < k; ++i) x[i] -= h * prev[q * ld + i];
+      }
     double nrm = 0.0;
     for (int i = 0; i < k; ++i) nrm += x[i] * x[i];
     const double inv = 1.0 / sqrt(nrm);
     for (int i = 0; i < k; ++i) x[i] *= inv;
   }
-  if (x[0] < 0.0)
+  if (n_prev == 0 && x[0] < 0.0)
     for (int i = 0; i < k; ++i) x[i] = -x[i];
 }
 
-// One warp.  Multisection: each round the 32 lanes count at 32 interior
-// points of [lo, hi] and the bracket shrinks 33-fold, until it is a few
-// ulps wide.  out[0] = theta, out[1] = |beta[k-1]| |s_k| (the Ritz residual
-// estimate).  With want_vec the eigenvector goes to s and out[0] is its
-// Rayleigh quotient; the vector is also formed when s_k is too small for
-// the minor ratio to resolve.
-__global__ void __launch_bounds__(32) tridiag_lowest_kernel(const double* __restrict__ alpha,
-                                                            const double* __restrict__ beta, int k, double* out,
-                                                            double* s, int want_vec) {
-  __shared__ double a[TRI_MAX], b[TRI_MAX], b2[TRI_MAX];
-  const int lane = threadIdx.x;
-  for (int i = lane; i < k; i += 32) {
-    a[i] = alpha[i];
-    const double bi = i < k - 1 ? beta[i] : 0.0;
-    b[i] = bi;
-    b2[i] = bi * bi;
-  }
-  __syncwarp();
-  // Gershgorin bracket
-  double lo = 1e300, hi = -1e300;
-  for (int i = lane; i < k; i += 32) {
-    const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + fabs(b[i]);
-    lo = fmin(lo, a[i] - r);
-    hi = fmax(hi, a[i] + r);
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-  }
-  const double span = hi - lo;
-  const double scale = fmax(fabs(lo), fabs(hi));
-  lo -= 1e-12 * span + 1e-300;
-  hi += 1e-12 * span + 1e-300;
+// Warp-collective multisection for the eigenvalue of index idx (0 = lowest):
+// on entry [lo, hi] holds it (count(lo) <= idx < count(hi)); each round the 32
+// lanes count at 32 interior points and the bracket shrinks 33-fold, until it
+// is a few ulps wide.  All lanes return the same bracket.
+__device__ void multisect(const double* a, const double* b2, int k, int idx, double& lo, double& hi) {
+  const int lane = threadIdx.x & 31;
   for (int round = 0; round < 64; ++round) {
     const double w = hi - lo;
     if (w <= 4.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 1e-300) break;
     const double x = lo + w * ((double)(lane + 1) * (1.0 / 33.0));
-    const unsigned above = __ballot_sync(0xffffffffu, sturm_minors(a, b2, k, x) >= 1);
+    const unsigned above = __ballot_sync(0xffffffffu, sturm_minors(a, b2, k, x) > idx);
     double nlo, nhi;
     if (above == 0u) {
       nlo = __shfl_sync(0xffffffffu, x, 31);
@@ -544,13 +539,55 @@ __global__ void __launch_bounds__(32) tridiag_lowest_kernel(const double* __rest
     lo = nlo;
     hi = nhi;
   }
-  if (lane != 0) return;
+}
+
+// Warp-collective: stage (a, b, b2) of the tridiagonal in shared memory and
+// return its Gershgorin bracket (widened) and scale.
+__device__ void stage_tridiag(const double* alpha, const double* beta, int k, double* a, double* b, double* b2,
+                              double& lo, double& hi, double& scale) {
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < k; i += 32) {
+    a[i] = alpha[i];
+    const double bi = i < k - 1 ? beta[i] : 0.0;
+    b[i] = bi;
+    b2[i] = bi * bi;
+  }
+  __syncwarp();
+  lo = 1e300;
+  hi = -1e300;
+  for (int i = lane; i < k; i += 32) {
+    const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + fabs(b[i]);
+    lo = fmin(lo, a[i] - r);
+    hi = fmax(hi, a[i] + r);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  const double span = hi - lo;
+  scale = fmax(fabs(lo), fabs(hi));
+  lo -= 1e-12 * span + 1e-300;
+  hi += 1e-12 * span + 1e-300;
+}
+
+// One warp.  out[0] = theta (lowest eigenvalue), out[1] = |beta[k-1]| |s_k|
+// (the Ritz residual estimate).  With want_vec the eigenvector goes to s and
+// out[0] is its Rayleigh quotient; the vector is also formed when s_k is
+// too small for the minor ratio to resolve.
+__global__ void __launch_bounds__(32) tridiag_lowest_kernel(const double* __restrict__ alpha,
+                                                            const double* __restrict__ beta, int k, double* out,
+                                                            double* s, int want_vec) {
+  __shared__ double a[TRI_MAX], b[TRI_MAX], b2[TRI_MAX];
+  double lo, hi, scale;
+  stage_tridiag(alpha, beta, k, a, b, b2, lo, hi, scale);
+  multisect(a, b2, k, 0, lo, hi);
+  if (threadIdx.x != 0) return;
   const double theta = 0.5 * (lo + hi);
   double sk = sqrt(last_component_sq(a, b2, k, theta));
   double th = theta;
   if (want_vec || sk < 1e-4) {
     double x[TRI_MAX];
-    inverse_iteration(a, b, k, theta, scale, want_vec ? 3 : 2, x);
+    inverse_iteration(a, b, k, theta, scale, want_vec ? 3 : 2, x, nullptr, 0, 0);
     sk = fabs(x[k - 1]);
     if (want_vec) {
       double rq = 0.0;
@@ -566,6 +603,108 @@ __global__ void __launch_bounds__(32) tridiag_lowest_kernel(const double* __rest
   }
   out[0] = th;
   out[1] = fabs(beta[k - 1]) * sk;
+}
+
+// Thick restart of a Lanczos cycle (Wu and Simon's thick-restart Lanczos).
+// From the k x k tridiagonal T (alpha, beta; beta[k-1] couples the residual
+// vector r) keep the m lowest Ritz pairs (theta_i, s_i).  Their couplings to
+// r are c_i = beta[k-1] s_i[k-1].  A Lanczos process on diag(theta) started
+// from c / |c| gives an orthogonal U (m x p) and a p x p tridiagonal; in
+// reversed order the kept vectors Z = V S U form a tridiagonal block whose
+// last vector alone couples to r with |c|, so the next cycle continues the
+// ordinary three-term recurrence from r at position p.  Writes C = S U
+// reversed (k x p, row-major: C[r * p + i]), alpha[0..p), beta[0..p) (beta[p-1]
+// = |c|) and *p_out.  One warp; serial parts in lane 0.
+__global__ void __launch_bounds__(32) lanczos_restart_kernel(double* alpha, double* beta, int k, int m, double* C,
+                                                             int* p_out) {
+  __shared__ double a[TRI_MAX], b[TRI_MAX], b2[TRI_MAX];
+  __shared__ double S[RESTART_MAX][TRI_MAX];
+  __shared__ double th[RESTART_MAX];
+  double glo, ghi, scale;
+  stage_tridiag(alpha, beta, k, a, b, b2, glo, ghi, scale);
+  if (m > k) m = k;
+  for (int i = 0; i < m; ++i) {
+    double lo = glo, hi = ghi;
+    multisect(a, b2, k, i, lo, hi);
+    if (threadIdx.x == 0) th[i] = 0.5 * (lo + hi);
+  }
+  __syncwarp();
+  if (threadIdx.x != 0) return;
+  const double bk = beta[k - 1];
+  double c[RESTART_MAX];
+  for (int i = 0; i < m; ++i) {
+    inverse_iteration(a, b, k, th[i], scale, 3, S[i], &S[0][0], TRI_MAX, i);
+    c[i] = bk * S[i][k - 1];
+  }
+  // Lanczos on diag(theta) from c / |c| with full reorthogonalisation
+  double cn = 0.0;
+  for (int i = 0; i < m; ++i) cn += c[i] * c[i];
+  cn = sqrt(cn);
+  double U[RESTART_MAX][RESTART_MAX];
+  double la[RESTART_MAX], lb[RESTART_MAX];
+  int p = 0;
+  if (cn > 0.0) {
+    for (int i = 0; i < m; ++i) U[0][i] = c[i] / cn;
+    p = 1;
+    for (int j = 0; j < m; ++j) {
+      double w[RESTART_MAX];
+      for (int i = 0; i < m; ++i) w[i] = th[i] * U[j][i];
+      double aj = 0.0;
+      for (int i = 0; i < m; ++i) aj += U[j][i] * w[i];
+      la[j] = aj;
+      for (int pass = 0; pass < 2; ++pass)
+        for (int q = 0; q <= j; ++q) {
+          double h = 0.0;
+          for (int i = 0; i < m; ++i) h += U[q][i] * w[i];
+          for (int i = 0; i < m; ++i) w[i] -= h * U[q][i];
+        }
+      double bj = 0.0;
+      for (int i = 0; i < m; ++i) bj += w[i] * w[i];
+      bj = sqrt(bj);
+      if (j + 1 >= m || bj <= 1e-13 * fmax(scale, 1e-300)) break;
+      lb[j] = bj;
+      for (int i = 0; i < m; ++i) U[j + 1][i] = w[i] / bj;
+      p = j + 2;
+    }
+  }
+  if (p == 0) {   // r decoupled: keep the lowest Ritz vector alone
+    p = 1;
+    for (int i = 0; i < m; ++i) U[0][i] = i == 0 ? 1.0 : 0.0;
+    la[0] = th[0];
+  }
+  // C[:, i] = S^T U[p-1-i] (reversed), new tridiagonal reversed
+  for (int r = 0; r < k; ++r)
+    for (int i = 0; i < p; ++i) {
+      double v = 0.0;
+      for (int q = 0; q < m; ++q) v += S[q][r] * U[p - 1 - i][q];
+      C[r * p + i] = v;
+    }
+  for (int i = 0; i < p; ++i) alpha[i] = la[p - 1 - i];
+  for (int i = 0; i + 1 < p; ++i) beta[i] = lb[p - 2 - i];
+  beta[p - 1] = cn;
+  *p_out = p;
+}
+
+// Z[:, i] = sum_r V[:, r] C[r * p + i] for i < p (p <= RESTART_MAX).
+__global__ void rotate_basis_kernel(const double* __restrict__ V, long long ld, int k, const double* __restrict__ C,
+                                    int p, double* __restrict__ Z, long long n) {
+  __shared__ double cs[TRI_MAX * RESTART_MAX];
+  for (int e = threadIdx.x; e < k * p; e += blockDim.x) cs[e] = C[e];
+  __syncthreads();
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double acc[RESTART_MAX];
+#pragma unroll
+    for (int q = 0; q < RESTART_MAX; ++q) acc[q] = 0.0;
+    for (int r = 0; r < k; ++r) {
+      const double v = V[(long long)r * ld + i];
+#pragma unroll
+      for (int q = 0; q < RESTART_MAX; ++q)
+        if (q < p) acc[q] = fma(cs[r * p + q], v, acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < RESTART_MAX; ++q)
+      if (q < p) Z[(long long)q * ld + i] = acc[q];
+  }
 }
 
 int grid_for(long long n) {
@@ -603,19 +742,19 @@ void launch_dot(const double* x, const double* y, long long n, double* partial, 
 }
 
 void launch_multidot(const double* Q, long long ldq, int k, const double* w, long long n, double* partial,
-                     double* out, cudaStream_t s) {
+                     double* out, cudaStream_t s, const double* gate_num, const double* gate_den, double ratio) {
   if (k <= 0) return;
   dim3 grid(RED_BLOCKS, k);
-  multidot_partial_kernel<<<grid, RED_THREADS, 0, s>>>(Q, ldq, k, w, n, partial);
+  multidot_partial_kernel<<<grid, RED_THREADS, 0, s>>>(Q, ldq, k, w, n, partial, gate_num, gate_den, ratio);
   count_launches(1);
-  finish_kernel<<<k, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, RED_BLOCKS, out);
+  finish_kernel<<<k, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, RED_BLOCKS, out, gate_num, gate_den, ratio);
   count_launches(1);
 }
 
 void launch_multiaxpy(const double* Q, long long ldq, int k, const double* c, double* w, long long n,
-                      cudaStream_t s) {
+                      cudaStream_t s, const double* gate_num, const double* gate_den, double ratio) {
   if (k <= 0) return;
-  multiaxpy_kernel<<<grid_for(n), 256, 0, s>>>(Q, ldq, k, c, w, n);
+  multiaxpy_kernel<<<grid_for(n), 256, 0, s>>>(Q, ldq, k, c, w, n, gate_num, gate_den, ratio);
   count_launches(1);
 }
 
@@ -690,6 +829,19 @@ void launch_cgs2_qr(double* X, const long long* xoff, const int* rows, const int
                     const long long* roff, int ldr, double dep_tol, double accept, cudaStream_t s) {
   if (count <= 0) return;
   cgs2_qr_kernel<<<count, QR_THREADS, 0, s>>>(X, xoff, rows, cols, R, roff, ldr, dep_tol, accept);
+  count_launches(1);
+}
+
+void launch_lanczos_restart(double* alpha, double* beta, int k, int m, double* C, int* p_out, cudaStream_t st) {
+  if (k <= 0 || k > TRI_MAX || m < 1 || m > RESTART_MAX) return;
+  lanczos_restart_kernel<<<1, 32, 0, st>>>(alpha, beta, k, m, C, p_out);
+  count_launches(1);
+}
+
+void launch_rotate_basis(const double* V, long long ld, int k, const double* C, int p, double* Z, long long n,
+                         cudaStream_t st) {
+  if (k <= 0 || k > TRI_MAX || p < 1 || p > RESTART_MAX) return;
+  rotate_basis_kernel<<<grid_for(n), 256, 0, st>>>(V, ld, k, C, p, Z, n);
   count_launches(1);
 }
 

@@ -361,6 +361,35 @@ std::vector<TreeNode> build_tree(int Lx, int Ly, int Lz) {
   return nodes;
 }
 
+// Node order of one sweep: layers from the bottom (Methods); inside a layer
+// a depth-first walk of the tree (first child first), the direction
+// alternating between consecutive layers.
+std::vector<int> sweep_order(const std::vector<TreeNode>& nodes) {
+  const int n = (int)nodes.size();
+  std::vector<int> rank(n, 0);
+  std::vector<int> stack{n - 1};
+  int next = 0;
+  while (!stack.empty()) {
+    const int i = stack.back();
+    stack.pop_back();
+    rank[i] = next++;
+    for (int c = 1; c >= 0; --c)
+      if (nodes[i].child_kind[c] == 1) stack.push_back(nodes[i].child[c]);
+  }
+  int top = 0;
+  for (const TreeNode& t : nodes) top = std::max(top, t.layer);
+  std::vector<int> order;
+  for (int layer = 0; layer <= top; ++layer) {
+    std::vector<int> row;
+    for (const TreeNode& t : nodes)
+      if (t.layer == layer) row.push_back(t.index);
+    std::sort(row.begin(), row.end(), [&](int a, int b) { return rank[a] < rank[b]; });
+    if (layer % 2 == 1) std::reverse(row.begin(), row.end());
+    order.insert(order.end(), row.begin(), row.end());
+  }
+  return order;
+}
+
 // ---------------------------------------------------------------- sectors
 Sectors physical_sectors(int parity) {
   Sectors s;

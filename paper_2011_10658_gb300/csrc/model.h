@@ -83,6 +83,9 @@ struct TreeNode {
 };
 
 std::vector<TreeNode> build_tree(int Lx, int Ly, int Lz);
+// Order of the node updates in one sweep (layers bottom-up, depth-first
+// inside a layer, direction alternating per layer).
+std::vector<int> sweep_order(const std::vector<TreeNode>& nodes);
 
 // Sector list of a bond: ascending charges with dimensions.
 struct Sectors {

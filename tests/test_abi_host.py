@@ -150,3 +150,8 @@ def test_model_errors(q):
         q.Model(2, 2, 2, boundary=1)
     with pytest.raises(QedError):
         q.Model(2, 2, 2, t=float("nan"))
+
+
+@pytest.mark.parametrize("L", [(2, 1, 1), (2, 2, 1), (2, 2, 2), (4, 4, 4), (8, 8, 8)])
+def test_sweep_order_equal(q, L):
+    assert q.Model(*L).sweep_order().tolist() == otree.sweep_order(otree.build_tree(*L))

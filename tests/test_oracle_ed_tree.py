@@ -235,3 +235,40 @@ def test_qr_sector_rank_deficient():
     assert np.sum(np.diag(R) == 0) == 3
     with pytest.raises(ValueError):
         tree.qr_sector(rng.standard_normal((3, 5)))
+
+
+def test_sweep_order_2x2x2_by_hand():
+    """2x2x2: bottom nodes 0,1 (children of 4) and 2,3 (children of 5) in
+    depth-first order, layer 1 walked backwards, then the root."""
+    assert tree.sweep_order(tree.build_tree(2, 2, 2)) == [0, 1, 2, 3, 5, 4, 6]
+
+
+@pytest.mark.parametrize("L", [(4, 4, 4), (8, 8, 8)])
+def test_sweep_order_properties(L):
+    """A permutation of the nodes, layers bottom-up, siblings adjacent in
+    the bottom layer, and fewer bond moves than number order."""
+    nodes = tree.build_tree(*L)
+    order = tree.sweep_order(nodes)
+    assert sorted(order) == list(range(len(nodes)))
+    layers = [nodes[i].layer for i in order]
+    assert layers == sorted(layers)
+    parent = {nd.index: nd.parent for nd in nodes}
+    bottom = [i for i in order if nodes[i].layer == 0]
+    for a, b in zip(bottom[0::2], bottom[1::2]):
+        assert parent[a] == parent[b]
+
+    def dist(a, b):
+        up = []
+        while a >= 0:
+            up.append(a)
+            a = parent[a]
+        steps = 0
+        while b not in up:
+            b = parent[b]
+            steps += 1
+        return steps + up.index(b)
+
+    def moves(seq):
+        return sum(dist(x, y) for x, y in zip([len(nodes) - 1] + list(seq[:-1]), seq))
+
+    assert moves(order) < moves(list(range(len(nodes))))
