@@ -121,19 +121,22 @@ void KPlan::finalize(long long k_part) {
   scratch_need = 0;
   // K per part: small enough that the launch has about four tiles per SM
   // when the plan has few, long contractions (a Gram matrix), at most k_part
-  long long work = 0;
+  long long work = 0, base_tiles = 0;
   for (const KOutput& o : outs) {
     long long ktot = 0;
     for (int c = o.chunk_begin; c < o.chunk_end; ++c) ktot += chunks[c].add ? 1 : chunks[c].K;
-    work += (long long)((o.M + KT_BM - 1) / KT_BM) * ((o.N + KT_BN - 1) / KT_BN) * ktot;
+    const long long t = (long long)((o.M + KT_BM - 1) / KT_BM) * ((o.N + KT_BN - 1) / KT_BN);
+    work += t * ktot;
+    base_tiles += t;
   }
   k_part = std::max(256LL, std::min(k_part, work / (4 * 152)));
+  const bool few_tiles = base_tiles < 4 * 152;
   for (size_t oi = 0; oi < outs.size(); ++oi) {
     KOutput& o = outs[oi];
     const int tm = (o.M + KT_BM - 1) / KT_BM, tn = (o.N + KT_BN - 1) / KT_BN;
     long long ktot = 0;
     for (int c = o.chunk_begin; c < o.chunk_end; ++c) ktot += chunks[c].add ? 1 : chunks[c].K;
-    const bool split = ktot > 2 * k_part && tm * tn <= 16;
+    const bool split = ktot > 2 * k_part && (tm * tn <= 16 || few_tiles);
     std::vector<std::pair<int, int>> parts;   // ranges in nc
     const int begin = (int)nc.size();
     if (!split) {
@@ -1913,7 +1916,9 @@ int Engine::optimize_node(int node, double tol, int max_krylov, SweepStats* st, 
   int iters = 0, mixed_iters = 0;
   if (mixed_node(node)) {
     cudaMemsetAsync(d_err_, 0, sizeof(int), stream_);
-    rc = lanczos(node, std::max(tol, mixed_tol), max_krylov, true, 50, &energy, &res, &mixed_iters);
+    // the low-precision phase aims a little below tol so that the FP64
+    // check usually passes on its first product
+    rc = lanczos(node, std::max(0.3 * tol, mixed_tol), max_krylov, true, 50, &energy, &res, &mixed_iters);
     if (rc) return rc;
     int herr = 0;
     cudaMemcpyAsync(&herr, d_err_, sizeof(int), cudaMemcpyDeviceToHost, stream_);
