@@ -223,6 +223,43 @@ int ttn_apply_heff(ttn_state *s, const double *x, double *y, int64_t n);
 /* Same with device buffers on the state's stream (no host copies). */
 int ttn_apply_heff_device(ttn_state *s, const double *x_device, double *y_device, int64_t n);
 
+/* Checkpoint.  ttn_save moves the centre to the root (so the file holds a
+ * tree isometric towards the root) and writes: the 8-byte tag "QEDTTN01",
+ * the model parameters (Lx, Ly, Lz, boundary, Q as int32; t, m, ge2, cB, nu as
+ * FP64), chi, precision (int32), seed (uint64), the node count (int32), the
+ * node sizes (int64) and every node tensor (FP64, the ttn_node_export
+ * layout), then an FNV-1a 64-bit hash of all preceding bytes; host byte
+ * order.  ttn_load checks the tag, the hash and that the parameters equal
+ * the model's (bitwise), creates a state on cuda_stream (ttn_create) and
+ * loads the tensors (ttn_load_tensors); QED_EINVAL on any mismatch or I/O
+ * error, *out NULL then.  Caller owns *out (ttn_destroy). */
+int ttn_save(ttn_state *s, const char *path);
+int ttn_load(const qed_model *m, const char *path, void *cuda_stream, ttn_state **out);
+
+/* Differentiation of E(psi; couplings) = psi^T H_eff psi / psi^T psi.
+ *
+ * y = H_eff^T x at the current centre with every product term transposed
+ * (A^T (x) B^T (x) C^T on the three legs, monomial site operators through
+ * inverse row maps): the hand-written adjoint of the H_eff contraction, FP64,
+ * device buffers (n doubles, centre layout) on the state's stream.  H_eff
+ * of Eq. (1) + Eq. (16) is real symmetric, so the result equals
+ * ttn_apply_heff_device's (FP64 state) to rounding. */
+int ttn_apply_heff_adjoint_device(ttn_state *s, const double *x_device, double *y_device, int64_t n);
+/* Energy gradient with the centre moved to `node` (node < 0: current
+ * centre).  psi_device: n doubles in the centre layout, or NULL for the
+ * centre tensor.  Outputs: *energy; dE_dpsi_device (optional, n doubles) =
+ * ((H + H^T) psi - 2 E psi) / psi^T psi, with H^T psi from the adjoint
+ * product; dE_dcoupling[5] = dE/d(t, m, ge2, cB, nu).  E is linear in the
+ * couplings, so each is the class expectation value divided by the coupling
+ * (Hellmann-Feynman); NaN for a zero coupling (its terms are absent).  The
+ * operator products are recomputed on every call (nothing is kept from an
+ * earlier call).  All products FP64 whatever the state's precision. */
+int ttn_energy_grad(ttn_state *s, int32_t node, const double *psi_device, int64_t n, double *energy,
+                    double *dE_dpsi_device, double dE_dcoupling[5]);
+/* Gradient node update on the centre tensor: psi <- (psi - eta dE/dpsi) /
+ * |psi - eta dE/dpsi|, with the energies before and after. */
+int ttn_gradient_step(ttn_state *s, double eta, double *e_before, double *e_after);
+
 /* y = H_eff x at the current centre, allocating nothing: no cudaMalloc,
  * cudaFree or other allocating routine is called, on the device or the
  * host.  The paper has no counterpart; this exists for callers whose

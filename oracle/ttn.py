@@ -446,3 +446,31 @@ def expectation(state: TTN, p: _model.Params):
         if nd.parent >= 0:
             other.up[nd.index] = other._up_ops(nd.index)
     return other.energy_at_center()
+
+
+def energy_gradient(state: TTN, X=None):
+    """E(X) = <X|H_eff|X> / <X|X> at the current centre (X defaults to the
+    centre tensor) and dE/dX = 2 (H_eff X - E X) / <X|X>: the gradient of a
+    Rayleigh quotient of the real symmetric H_eff of Eq. (1) + Eq. (16).
+    Test infrastructure (differentiation row)."""
+    idx = state.center
+    if X is None:
+        X = state.T[idx]
+    HX = state.heff_apply(idx, X)
+    nrm = float(np.vdot(X, X))
+    e = float(np.vdot(X, HX)) / nrm
+    return e, 2.0 * (HX - e * X) / nrm
+
+
+COUPLINGS = ("t", "m", "ge2", "cB", "nu")
+
+
+def coupling_gradient(state: TTN, p: _model.Params):
+    """dE/dc for c in (t, m, ge2, cB, nu) at fixed tensors.  Eq. (1) + Eq. (16)
+    is linear in each coupling, so dE/dc = <H_c> / c with H_c the terms of
+    class c (Hellmann-Feynman); NaN for a zero coupling."""
+    out = {}
+    for c in COUPLINGS:
+        val = getattr(p, c)
+        out[c] = expectation(state, _model.class_only(p, c)) / val if val != 0.0 else float("nan")
+    return out

@@ -234,6 +234,41 @@ class TTN:
     def apply_heff_device(self, x_ptr, y_ptr, n):
         check(lib().ttn_apply_heff_device(self._h, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), n))
 
+    def save(self, path):
+        """Checkpoint (centre moved to the root first); see ttn_save."""
+        check(lib().ttn_save(self._h, str(path).encode()))
+
+    @classmethod
+    def load(cls, model, path, stream=None):
+        """State read from a ttn_save file for the same model."""
+        h = ctypes.c_void_p()
+        check(lib().ttn_load(model.handle, str(path).encode(), ctypes.c_void_p(stream or 0), ctypes.byref(h)))
+        obj = cls.__new__(cls)
+        obj.model = model
+        obj._h = h
+        obj.chi = None
+        return obj
+
+    def apply_heff_adjoint_device(self, x_ptr, y_ptr, n):
+        """y = H_eff^T x (transposed terms, FP64) on device buffers."""
+        check(lib().ttn_apply_heff_adjoint_device(self._h, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), n))
+
+    def energy_grad_device(self, node=-1, psi_ptr=None, grad_ptr=None, n=0):
+        """(E, {class: dE/dcoupling}) with the centre moved to ``node``, for the
+        device vector at psi_ptr (n doubles) or the centre tensor; dE/dpsi is
+        written to grad_ptr when given."""
+        e = ctypes.c_double()
+        dc = np.zeros(5)
+        check(lib().ttn_energy_grad(self._h, node, ctypes.c_void_p(psi_ptr or 0), n, ctypes.byref(e),
+                                    ctypes.c_void_p(grad_ptr or 0), _ptr(dc, ctypes.c_double)))
+        return e.value, dict(zip(CLASSES, dc.tolist()))
+
+    def gradient_step(self, eta):
+        """psi <- normalize(psi - eta dE/dpsi) on the centre tensor; (E before, E after)."""
+        e0, e1 = ctypes.c_double(), ctypes.c_double()
+        check(lib().ttn_gradient_step(self._h, eta, ctypes.byref(e0), ctypes.byref(e1)))
+        return e0.value, e1.value
+
     def apply_heff_device_noalloc(self, x_ptr, y_ptr, n):
         """Same product as apply_heff_device in FP64 at a bottom-node centre,
         with no memory allocated by the call (see include/qedttn.h)."""

@@ -66,6 +66,11 @@ SIGNATURES = [
     ("qed_launch_count", c_int, [c_int64_p]),
     ("ttn_apply_heff", c_int, [c_void_p, c_double_p, c_double_p, c_int64]),
     ("ttn_apply_heff_device", c_int, [c_void_p, c_void_p, c_void_p, c_int64]),
+    ("ttn_save", c_int, [c_void_p, ctypes.c_char_p]),
+    ("ttn_load", c_int, [c_void_p, ctypes.c_char_p, c_void_p, ctypes.POINTER(c_void_p)]),
+    ("ttn_apply_heff_adjoint_device", c_int, [c_void_p, c_void_p, c_void_p, c_int64]),
+    ("ttn_energy_grad", c_int, [c_void_p, c_int32, c_void_p, c_int64, c_double_p, c_void_p, c_double_p]),
+    ("ttn_gradient_step", c_int, [c_void_p, c_double, c_double_p, c_double_p]),
     ("ttn_apply_heff_device_noalloc", c_int, [c_void_p, c_void_p, c_void_p, c_int64]),
 ]
 

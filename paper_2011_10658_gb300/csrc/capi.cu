@@ -1,6 +1,7 @@
 // C ABI of the qedttn library (see include/qedttn.h for the contract).
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <exception>
 #include <string>
@@ -506,6 +507,153 @@ QED_API int ttn_apply_heff_device(ttn_state* s, const double* x_device, double* 
   if (!s || !x_device || !y_device) return fail(QED_EINVAL, "null argument");
   if (n != s->engine->node_size(s->engine->center())) return fail(QED_EINVAL, "size must equal the centre tensor size");
   QED_TRY(return engine_status(s->engine, s->engine->apply_heff_native(x_device, y_device));)
+}
+
+namespace {
+const char kCkptTag[8] = {'Q', 'E', 'D', 'T', 'T', 'N', '0', '1'};
+
+struct Fnv {
+  uint64_t h = 1469598103934665603ull;
+  void add(const void* p, size_t n) {
+    const unsigned char* b = (const unsigned char*)p;
+    for (size_t i = 0; i < n; ++i) { h ^= b[i]; h *= 1099511628211ull; }
+  }
+};
+
+bool write_all(FILE* f, Fnv* fnv, const void* p, size_t n) {
+  if (fnv) fnv->add(p, n);
+  return std::fwrite(p, 1, n, f) == n;
+}
+
+bool read_all(FILE* f, Fnv* fnv, void* p, size_t n) {
+  if (std::fread(p, 1, n, f) != n) return false;
+  if (fnv) fnv->add(p, n);
+  return true;
+}
+
+struct CkptHeader {
+  int32_t L[3], boundary, Q;
+  double c[5];
+  int32_t chi, precision;
+  uint64_t seed;
+  int32_t n_nodes;
+};
+
+bool read_header(FILE* f, Fnv* fnv, CkptHeader* h) {
+  char tag[8];
+  if (!read_all(f, fnv, tag, 8) || std::memcmp(tag, kCkptTag, 8) != 0) return false;
+  return read_all(f, fnv, h->L, sizeof(h->L)) && read_all(f, fnv, &h->boundary, 4) && read_all(f, fnv, &h->Q, 4) &&
+         read_all(f, fnv, h->c, sizeof(h->c)) && read_all(f, fnv, &h->chi, 4) &&
+         read_all(f, fnv, &h->precision, 4) && read_all(f, fnv, &h->seed, 8) && read_all(f, fnv, &h->n_nodes, 4);
+}
+}  // namespace
+
+QED_API int ttn_save(ttn_state* s, const char* path) {
+  if (!s || !path) return fail(QED_EINVAL, "null argument");
+  QED_TRY(
+    qed::Engine* e = s->engine;
+    int rc = e->move_to(e->n_nodes() - 1);
+    if (rc) return engine_status(e, rc);
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(QED_EINVAL, "cannot open the checkpoint file for writing");
+    Fnv fnv;
+    const qed::Params& p = s->model->p;
+    const int32_t L[3] = {p.Lx, p.Ly, p.Lz};
+    const double c[5] = {p.t, p.m, p.ge2, p.cB, p.nu};
+    const int32_t chi = e->chi(), prec = e->precision(), nn = e->n_nodes();
+    const uint64_t seed = e->seed();
+    bool ok = write_all(f, &fnv, kCkptTag, 8) && write_all(f, &fnv, L, sizeof(L)) &&
+              write_all(f, &fnv, &p.boundary, 4) && write_all(f, &fnv, &p.Q, 4) && write_all(f, &fnv, c, sizeof(c)) &&
+              write_all(f, &fnv, &chi, 4) && write_all(f, &fnv, &prec, 4) && write_all(f, &fnv, &seed, 8) &&
+              write_all(f, &fnv, &nn, 4);
+    for (int i = 0; ok && i < nn; ++i) {
+      const int64_t n = e->node_size(i);
+      ok = write_all(f, &fnv, &n, 8);
+    }
+    std::vector<double> buf;
+    for (int i = 0; ok && i < nn; ++i) {
+      rc = e->node_export(i, &buf);
+      if (rc) { std::fclose(f); return engine_status(e, rc); }
+      ok = write_all(f, &fnv, buf.data(), buf.size() * sizeof(double));
+    }
+    ok = ok && write_all(f, nullptr, &fnv.h, 8);
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(QED_EINVAL, "checkpoint write failed");
+    return QED_OK;
+  )
+}
+
+QED_API int ttn_load(const qed_model* m, const char* path, void* cuda_stream, ttn_state** out) {
+  if (!m || !path || !out) return fail(QED_EINVAL, "null argument");
+  *out = nullptr;
+  QED_TRY(
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(QED_EINVAL, "cannot open the checkpoint file");
+    Fnv fnv;
+    CkptHeader h;
+    if (!read_header(f, &fnv, &h)) { std::fclose(f); return fail(QED_EINVAL, "not a checkpoint file"); }
+    const qed::Params& p = m->p;
+    const double c[5] = {p.t, p.m, p.ge2, p.cB, p.nu};
+    if (h.L[0] != p.Lx || h.L[1] != p.Ly || h.L[2] != p.Lz || h.boundary != p.boundary || h.Q != p.Q ||
+        std::memcmp(h.c, c, sizeof(c)) != 0 || h.n_nodes != (int32_t)m->nodes.size()) {
+      std::fclose(f);
+      return fail(QED_EINVAL, "checkpoint parameters differ from the model");
+    }
+    std::vector<int64_t> sizes(h.n_nodes);
+    bool ok = true;
+    for (int i = 0; ok && i < h.n_nodes; ++i) ok = read_all(f, &fnv, &sizes[i], 8) && sizes[i] >= 0 && sizes[i] < (1LL << 40);
+    std::vector<std::vector<double>> data(h.n_nodes);
+    for (int i = 0; ok && i < h.n_nodes; ++i) {
+      data[i].resize(sizes[i]);
+      ok = read_all(f, &fnv, data[i].data(), sizes[i] * sizeof(double));
+    }
+    uint64_t stored = 0;
+    ok = ok && read_all(f, nullptr, &stored, 8) && stored == fnv.h;
+    std::fclose(f);
+    if (!ok) return fail(QED_EINVAL, "checkpoint truncated or corrupt");
+    ttn_state* s = nullptr;
+    int rc = ttn_create(m, h.chi, h.seed, h.precision, cuda_stream, &s);
+    if (rc) return rc;
+    std::vector<const double*> ptrs(h.n_nodes);
+    for (int i = 0; i < h.n_nodes; ++i) ptrs[i] = data[i].data();
+    rc = ttn_load_tensors(s, ptrs.data(), sizes.data(), h.n_nodes);
+    if (rc) { ttn_destroy(s); return rc; }
+    *out = s;
+    return QED_OK;
+  )
+}
+
+QED_API int ttn_apply_heff_adjoint_device(ttn_state* s, const double* x_device, double* y_device, int64_t n) {
+  if (!s || !x_device || !y_device) return fail(QED_EINVAL, "null argument");
+  if (n != s->engine->node_size(s->engine->center())) return fail(QED_EINVAL, "size must equal the centre tensor size");
+  QED_TRY(return engine_status(s->engine, s->engine->apply_heff_adjoint(x_device, y_device));)
+}
+
+QED_API int ttn_energy_grad(ttn_state* s, int32_t node, const double* psi_device, int64_t n, double* energy,
+                            double* dE_dpsi_device, double dE_dcoupling[5]) {
+  if (!s || !dE_dcoupling) return fail(QED_EINVAL, "null argument");
+  if (node >= s->engine->n_nodes()) return fail(QED_EINVAL, "node out of range");
+  QED_TRY(
+    if (node >= 0) {
+      int rc = s->engine->move_to(node);
+      if (rc) return engine_status(s->engine, rc);
+    }
+    if (psi_device && n != s->engine->node_size(s->engine->center()))
+      return fail(QED_EINVAL, "size must equal the centre tensor size");
+    if (dE_dpsi_device && n != s->engine->node_size(s->engine->center()))
+      return fail(QED_EINVAL, "size must equal the centre tensor size");
+    double e = 0.0;
+    int rc = s->engine->energy_grad(psi_device, &e, dE_dpsi_device, dE_dcoupling);
+    if (rc) return engine_status(s->engine, rc);
+    if (energy) *energy = e;
+    return QED_OK;
+  )
+}
+
+QED_API int ttn_gradient_step(ttn_state* s, double eta, double* e_before, double* e_after) {
+  if (!s) return fail(QED_EINVAL, "null argument");
+  if (!std::isfinite(eta)) return fail(QED_EINVAL, "eta must be finite");
+  QED_TRY(return engine_status(s->engine, s->engine->gradient_step(eta, e_before, e_after));)
 }
 
 }  // extern "C"

@@ -478,6 +478,9 @@ Engine::Engine(const Params& p, int chi, uint64_t seed, int precision, cudaStrea
   x_in_ = (double*)dalloc(nmax_ * sizeof(double));
   y_out_ = (double*)dalloc(nmax_ * sizeof(double));
   tmp_ = (double*)dalloc(nmax_ * sizeof(double));
+  grad_a_ = (double*)dalloc(nmax_ * sizeof(double));
+  grad_b_ = (double*)dalloc(nmax_ * sizeof(double));
+  grad_c_ = (double*)dalloc(nmax_ * sizeof(double));
   d_scal_ = (double*)dalloc(8192 * sizeof(double));
   d_partial_ = (double*)dalloc(304 * (kMaxKrylov + 2) * sizeof(double));
   d_err_ = (int*)dalloc(4 * sizeof(int));   // [0] tensor-core wait flag, [1] thick-restart count
@@ -606,6 +609,43 @@ const std::vector<RowMap>& Engine::rowmap(int node, int term) {
   for (size_t oc = 0; oc < layout_[node].leg[2].q.size(); ++oc)
     maps.push_back(build_rowmap_sector(node, A, B, (int)oc, nullptr));
   return rowmaps_[key] = maps;
+}
+
+// Inverse of a monomial row map (the transposed operator): for each row r'
+// of the source sector, the output row r with map(r) = r' and the same sign
+// and factor, or none.  Built on the host from the device map, cached.
+const RowMap& Engine::inverse_rowmap(const RowMap& fwd, int rows_fwd, int rows_inv) {
+  auto it = inv_maps_.find(fwd.map);
+  if (it != inv_maps_.end()) return it->second;
+  std::vector<int> m(std::max(rows_fwd, 1));
+  std::vector<double> v;
+  cudaMemcpyAsync(m.data(), fwd.map, rows_fwd * sizeof(int), cudaMemcpyDeviceToHost, stream_);
+  if (fwd.val) {
+    v.resize(std::max(rows_fwd, 1));
+    cudaMemcpyAsync(v.data(), fwd.val, rows_fwd * sizeof(double), cudaMemcpyDeviceToHost, stream_);
+  }
+  cudaStreamSynchronize(stream_);
+  std::vector<int> im(std::max(rows_inv, 1), -1);
+  std::vector<double> iv(fwd.val ? std::max(rows_inv, 1) : 0, 0.0);
+  long long nnz = 0;
+  for (int r = 0; r < rows_fwd; ++r) {
+    if (m[r] < 0) continue;
+    const int src = m[r] >> 1;
+    im[src] = (r << 1) | (m[r] & 1);
+    if (fwd.val) iv[src] = v[r];
+    ++nnz;
+  }
+  RowMap inv;
+  inv.src_sector = -2;   // not used for inverse maps
+  inv.nnz = nnz;
+  inv.map = (int*)dalloc(im.size() * sizeof(int));
+  cudaMemcpyAsync(inv.map, im.data(), im.size() * sizeof(int), cudaMemcpyHostToDevice, stream_);
+  if (fwd.val) {
+    inv.val = (double*)dalloc(iv.size() * sizeof(double));
+    cudaMemcpyAsync(inv.val, iv.data(), iv.size() * sizeof(double), cudaMemcpyHostToDevice, stream_);
+  }
+  cudaStreamSynchronize(stream_);
+  return inv_maps_[fwd.map] = inv;
 }
 
 // Diagonal site Hamiltonian (single-site terms, one class or all) on a leg.
@@ -1339,8 +1379,10 @@ void Engine::build_heff_terms(int node, int cls, std::vector<HTerm>* out) {
 
 // H_eff plans of (node, class filter), built on first use and replayed.
 // Returns nullptr (err_ set) if validation fails.
-Engine::HeffPlans* Engine::heff_plans(int node, int cls) {
-  const auto key = std::make_pair(node, cls);
+// adjoint: the transposed operator (every term applied as A^T (x) B^T (x) C^T),
+// FP64 only; cached under a separate key.
+Engine::HeffPlans* Engine::heff_plans(int node, int cls, bool adjoint) {
+  const auto key = std::make_pair(node, adjoint ? cls - 1000 : cls);
   auto hit = heff_cache_.find(key);
   if (hit != heff_cache_.end()) return hit->second.get();
   std::unique_ptr<HeffPlans> hp(new HeffPlans);
@@ -1352,7 +1394,57 @@ Engine::HeffPlans* Engine::heff_plans(int node, int cls) {
   KPlan& s3 = st[2];
   const int d2 = L.leg[2].total();
   const double cst = (cls < 0 || cls == CLS_NU) ? constant_ : 0.0;
-  if (bottom) {
+  if (bottom && adjoint) {
+    // transposed terms: the forward chunk y_oc += x_ic[map] C[oc, ic]^T becomes
+    // y_ic += x_oc[inverse map] C[oc, ic]
+    for (size_t oc = 0; oc < L.leg[2].q.size(); ++oc) {
+      const int rows = L.sec_rows[oc];
+      if (rows == 0) continue;
+      const int dc = L.leg[2].dim[oc];
+      s3.add_output(y_out_ + L.sec_off[oc], dc, 1, rows, dc, 0);
+      if (cst != 0.0) {
+        KChunk c = make_chunk();
+        c.A = x_in_ + L.sec_off[oc]; c.a_m = dc; c.a_k = 1;
+        c.add = 1; c.alpha = cst;
+        s3.add_chunk(c);
+      }
+    }
+    for (size_t oc = 0; oc < L.leg[2].q.size(); ++oc) {
+      if (L.sec_rows[oc] == 0) continue;
+      const int dco = L.leg[2].dim[oc];
+      for (const HTerm& h : hts) {
+        const bool phys = h.op[0].kind == 2 || h.op[1].kind == 2;
+        const RowMap* rm = nullptr;
+        if (phys) {
+          if (h.op[0].kind == 2 && h.op[0].term < 0) rm = &site_ham_map(node, 0, h.op[0].cls)[oc];
+          else if (h.op[1].kind == 2 && h.op[1].term < 0) rm = &site_ham_map(node, 1, h.op[1].cls)[oc];
+          else rm = &rowmap(node, h.op[0].kind == 2 ? h.op[0].term : h.op[1].term)[oc];
+          if (rm->src_sector < 0) continue;
+        }
+        const int ic = phys ? rm->src_sector : (int)oc;
+        if (L.sec_rows[ic] == 0) continue;
+        const int dci = L.leg[2].dim[ic];
+        KChunk c = make_chunk();
+        c.A = x_in_ + L.sec_off[oc]; c.a_m = dco; c.a_k = 1;
+        if (rm) {
+          const RowMap& inv = inverse_rowmap(*rm, L.sec_rows[oc], L.sec_rows[ic]);
+          c.amap = inv.map; c.aval = inv.val;
+        }
+        c.alpha = h.coef;
+        if (h.op[2].kind == 1) {
+          if (L.leg[2].find(L.leg[2].q[ic] + h.op[2].shift) != (int)oc) continue;
+          c.B = h.op[2].ptr + L.leg[2].offset((int)oc) * d2 + L.leg[2].offset(ic);
+          c.b_k = d2; c.b_n = 1;
+          c.K = dco;
+        } else {
+          if (ic != (int)oc) continue;
+          c.add = 1;
+        }
+        s3.add_output(y_out_ + L.sec_off[ic], dci, 1, L.sec_rows[ic], dci, 0);
+        s3.add_chunk(c);
+      }
+    }
+  } else if (bottom) {
     // per output c-sector: chunks over terms, A rows gathered from x_in
     for (size_t oc = 0; oc < L.leg[2].q.size(); ++oc) {
       const int rows = L.sec_rows[oc];
@@ -1409,28 +1501,28 @@ Engine::HeffPlans* Engine::heff_plans(int node, int cls) {
     struct Src { const double* Z; int shift; };
     std::vector<Src> srcs;
     int zi = 0;
+    // the adjoint applies each operator transposed, which reverses its shift
+    const int sg = adjoint ? -1 : 1;
     for (const HTerm& h : hts) {
       const double* Z = x_in_;
       int shift = 0;
+      const int sh0 = sg * h.op[0].shift, sh1 = sg * h.op[1].shift;
       if (h.op[0].kind) {
         double* z1 = zpool_ + (zi++) * zsize;
-        plan_leg_apply(st[0], L, x_in_, lays[h.op[0].shift], z1, 0, h.op[0].ptr, dl, h.op[0].shift, false,
-                       1.0);
+        plan_leg_apply(st[0], L, x_in_, lays[sh0], z1, 0, h.op[0].ptr, dl, sh0, adjoint, 1.0);
         Z = z1;
-        shift = h.op[0].shift;
+        shift = sh0;
         if (h.op[1].kind) {
           double* z2 = zpool_ + (zi++) * zsize;
-          plan_leg_apply(st[1], lays[shift], z1, lays[shift + h.op[1].shift], z2, 1, h.op[1].ptr, dr,
-                         h.op[1].shift, false, 1.0);
+          plan_leg_apply(st[1], lays[shift], z1, lays[shift + sh1], z2, 1, h.op[1].ptr, dr, sh1, adjoint, 1.0);
           Z = z2;
-          shift += h.op[1].shift;
+          shift += sh1;
         }
       } else if (h.op[1].kind) {
         double* z1 = zpool_ + (zi++) * zsize;
-        plan_leg_apply(st[0], L, x_in_, lays[h.op[1].shift], z1, 1, h.op[1].ptr, dr, h.op[1].shift, false,
-                       1.0);
+        plan_leg_apply(st[0], L, x_in_, lays[sh1], z1, 1, h.op[1].ptr, dr, sh1, adjoint, 1.0);
         Z = z1;
-        shift = h.op[1].shift;
+        shift = sh1;
       }
       srcs.push_back({Z, shift});
     }
@@ -1452,7 +1544,13 @@ Engine::HeffPlans* Engine::heff_plans(int node, int cls) {
         KChunk c = make_chunk();
         c.A = srcs[t].Z + zb.off; c.a_m = zb.dc; c.a_k = 1;
         c.alpha = h.coef;
-        if (h.op[2].kind == 1) {
+        if (h.op[2].kind == 1 && adjoint) {
+          // C^T: y_c' = sum_c C[c, c'] Z_c, C mapping sector yb.ic to zb.ic
+          if (L.leg[2].find(L.leg[2].q[yb.ic] + h.op[2].shift) != zb.ic) continue;
+          c.B = h.op[2].ptr + L.leg[2].offset(zb.ic) * d2 + L.leg[2].offset(yb.ic);
+          c.b_k = d2; c.b_n = 1;
+          c.K = zb.dc;
+        } else if (h.op[2].kind == 1) {
           if (L.leg[2].find(L.leg[2].q[zb.ic] + h.op[2].shift) != yb.ic) continue;
           c.B = h.op[2].ptr + L.leg[2].offset(yb.ic) * d2 + L.leg[2].offset(zb.ic);
           c.b_k = 1; c.b_n = d2;
@@ -1498,7 +1596,7 @@ int Engine::apply_heff(const double* x, double* y, int cls) {
     if (y != y_out_) launch_copy(y_out_, y, n, stream_);
     return check(cudaGetLastError(), "apply_heff (mixed)") ? 0 : -3;
   }
-  HeffPlans* hp = heff_plans(center_, cls);
+  HeffPlans* hp = heff_plans(center_, cls, false);
   if (!hp) return -1;
   ensure_scratch(std::max<long long>(hp->scratch_need, 1));
   if (x != x_in_) launch_copy(x, x_in_, n, stream_);
@@ -1518,6 +1616,88 @@ int Engine::apply_heff(const double* x, double* y, int cls) {
   if (profiling_) ev_end(e0, bottom ? KC_HEFF_SIMT_BOTTOM : KC_HEFF_SIMT_UPPER, hp->flops, hp->flops, 0.0);
   if (y != y_out_) launch_copy(y_out_, y, n, stream_);
   return check(cudaGetLastError(), "apply_heff") ? 0 : -3;
+}
+
+// y = H_eff^T x at the current centre: the hand-written adjoint of the
+// contraction (each term transposed), FP64.  H_eff is symmetric, so this
+// equals apply_heff up to rounding; the energy gradient uses both.
+int Engine::apply_heff_adjoint(const double* x, double* y) {
+  const long long n = layout_[center_].size;
+  const bool bottom = nodes_[center_].child_kind[0] == 0;
+  HeffPlans* hp = heff_plans(center_, -1, true);
+  if (!hp) return -1;
+  ensure_scratch(std::max<long long>(hp->scratch_need, 1));
+  if (x != x_in_) launch_copy(x, x_in_, n, stream_);
+  if (!bottom && hp->z_elems > 0) cudaMemsetAsync(zpool_, 0, hp->z_elems * sizeof(double), stream_);
+  for (int i = 0; i < 3; ++i) {
+    KPlan& pl = hp->st[i];
+    if (pl.tiles.empty()) continue;
+    launch_kc_gemm(pl.d_tiles, (int)pl.tiles.size(), pl.d_outs, pl.d_chunks, scratch_, stream_, 0);
+    launch_kc_reduce(pl.d_outs, (int)pl.outs.size(), pl.d_red, (int)pl.red.size(), scratch_, stream_);
+  }
+  if (y != y_out_) launch_copy(y_out_, y, n, stream_);
+  return check(cudaGetLastError(), "apply_heff_adjoint") ? 0 : -3;
+}
+
+// E(psi) = psi^T H_eff psi / psi^T psi at the centre (psi = the centre tensor
+// when psi == nullptr).  grad (device, optional) = dE/dpsi = ((H + H^T) psi -
+// 2 E psi) / psi^T psi.  dE/dc per coupling class: E is linear in the
+// couplings (Eq. (1) + Eq. (16)), so dE/dc = <psi|H_c|psi> / (c <psi|psi>),
+// the Hellmann-Feynman value; NaN where the coupling is zero (its terms are
+// not in the model).  Every product runs in FP64.
+int Engine::energy_grad(const double* psi, double* energy, double* grad, double dc[N_CLASSES]) {
+  const long long n = layout_[center_].size;
+  const double* x = psi ? psi : T_[center_];
+  double* hx = grad_a_;
+  double* htx = grad_b_;
+  double* dv = d_scal_ + 700;   // [0] |psi|^2, [1] psi.H psi, [2..6] classes
+  int rc = 0;
+  launch_dot(x, x, n, d_partial_, dv, stream_);
+  if ((rc = apply_heff(x, hx, -1))) return rc;
+  launch_dot(x, hx, n, d_partial_, dv + 1, stream_);
+  for (int c = 0; c < N_CLASSES; ++c) {
+    if ((rc = apply_heff(x, y_out_, c))) return rc;
+    launch_dot(x, y_out_, n, d_partial_, dv + 2 + c, stream_);
+  }
+  double host[8];
+  cudaMemcpyAsync(host, dv, 7 * sizeof(double), cudaMemcpyDeviceToHost, stream_);
+  if (!check(cudaStreamSynchronize(stream_), "energy gradient")) return -3;
+  const double nrm = host[0];
+  if (!(nrm > 0.0)) { err_ = "energy gradient: zero vector"; return -1; }
+  const double e = host[1] / nrm;
+  if (energy) *energy = e;
+  const double coupling[N_CLASSES] = {p_.t, p_.m, p_.ge2, p_.cB, p_.nu};
+  for (int c = 0; c < N_CLASSES; ++c)
+    dc[c] = coupling[c] != 0.0 ? host[2 + c] / nrm / coupling[c] : std::nan("");
+  if (grad) {
+    if ((rc = apply_heff_adjoint(x, htx))) return rc;
+    // grad = (hx + htx - 2 e x) / nrm
+    launch_add_scaled(htx, hx, n, 1.0, stream_);
+    launch_copy(hx, grad, n, stream_);
+    launch_axpby(x, grad, n, nullptr, -2.0 * e / nrm, 1.0, nullptr, 1.0 / nrm, stream_);
+    if (!check(cudaStreamSynchronize(stream_), "energy gradient")) return -3;
+  }
+  return check(cudaGetLastError(), "energy gradient") ? 0 : -3;
+}
+
+// One gradient step on the centre tensor: psi <- (psi - eta dE/dpsi) /
+// |psi - eta dE/dpsi|, energies before and after.
+int Engine::gradient_step(double eta, double* e_before, double* e_after) {
+  const long long n = layout_[center_].size;
+  double dc[N_CLASSES];
+  double e0 = 0.0;
+  int rc = energy_grad(nullptr, &e0, grad_c_, dc);
+  if (rc) return rc;
+  launch_axpby(grad_c_, T_[center_], n, nullptr, -eta, 1.0, nullptr, 1.0, stream_);
+  double* nrm2 = d_scal_ + 640;
+  launch_dot(T_[center_], T_[center_], n, d_partial_, nrm2, stream_);
+  launch_scale_inv_sqrt(T_[center_], T_[center_], n, nrm2, stream_);
+  double e1 = 0.0;
+  rc = energy_grad(nullptr, &e1, nullptr, dc);
+  if (rc) return rc;
+  if (e_before) *e_before = e0;
+  if (e_after) *e_after = e1;
+  return 0;
 }
 
 // ------------------------------------------------------------------ mixed precision

@@ -186,6 +186,13 @@ class Engine {
   int optimize_node(int node, double tol, int max_krylov, SweepStats* st, double* e);
   // H_eff x at the current centre (x, y device pointers, centre layout).
   int apply_heff(const double* x, double* y, int cls_filter);
+  // y = H_eff^T x (transposed terms, FP64) at the current centre.
+  int apply_heff_adjoint(const double* x, double* y);
+  // Energy, dE/dpsi (device, optional) and dE/dcoupling[5] at the centre for
+  // psi (device, centre layout) or the centre tensor when psi == nullptr.
+  int energy_grad(const double* psi, double* energy, double* grad, double dc[N_CLASSES]);
+  // psi <- normalize(psi - eta dE/dpsi) on the centre tensor.
+  int gradient_step(double eta, double* e_before, double* e_after);
   // H_eff x in the state's precision (tensor cores at bottom nodes when mixed)
   int apply_heff_native(const double* x, double* y) {
     use_mixed_ = precision_ != PREC_FP64;
@@ -213,6 +220,8 @@ class Engine {
   int kernel_timing(KernelTiming out[KC_COUNT]);
   void reset_timing();
   int precision() const { return precision_; }
+  int chi() const { return chi_; }
+  uint64_t seed() const { return seed_; }
   void set_precision(int p);
   // mixed path tuning: residual target of the low-precision phase
   double mixed_tol = 0.0;
@@ -264,7 +273,12 @@ class Engine {
     double flops = 0.0;          // algorithmic flops of one product
   };
   std::map<std::pair<int, int>, std::unique_ptr<HeffPlans>> heff_cache_;
-  HeffPlans* heff_plans(int node, int cls_filter);
+  HeffPlans* heff_plans(int node, int cls_filter, bool adjoint);
+  std::map<const int*, RowMap> inv_maps_;   // inverse row maps of the adjoint
+  const RowMap& inverse_rowmap(const RowMap& fwd, int rows_fwd, int rows_inv);
+  double* grad_a_ = nullptr;
+  double* grad_b_ = nullptr;
+  double* grad_c_ = nullptr;
   // persistent QR / move buffers (largest bond dimension squared)
   double* qr_G_ = nullptr;
   double* qr_Rinv_ = nullptr;
