@@ -266,7 +266,7 @@ def run_native(args):
     elapsed_ms = ev0.elapsed_time(ev1)
     launches = q.launch_count() - launches0
     clocks = sampler.stop()
-    kt = {k: s.kernel_timing(k) for k in ("tc_heff", "heff_simt_bottom", "heff_simt_upper", "move", "lanczos")}
+    kt = {k: s.kernel_timing(k) for k in ("tc_heff", "heff_simt_bottom", "heff_simt_upper", "move", "lanczos", "move_qr", "move_ops")}
     flops = sum(kt[k]["flops_alg"] for k in ("tc_heff", "heff_simt_bottom", "heff_simt_upper"))
     if world > 1:
         t = torch.tensor([elapsed_ms, flops], device="cuda", dtype=torch.float64)

@@ -163,7 +163,9 @@ int ttn_last_update(ttn_state *s, int32_t *iters_fp64, int32_t *iters_mixed, dou
  * H_eff (FP64), 2 = SIMT upper-node H_eff (FP64, or FP32 in the
  * low-precision phase of a mixed state), 3 = whole centre moves (QR,
  * R absorption, operator updates), 4 = whole Lanczos calls (products
- * included; the difference is vector work and idle time).  Returns accumulated milliseconds,
+ * included; the difference is vector work and idle time), 5 = per-bond QR
+ * and R absorption of a move, 6 = per-bond operator update of a move
+ * (FP64; flops = its grouped-GEMM chunks).  Returns accumulated milliseconds,
  * launches, algorithmic flops (nonzero rows of the monomial gathers times
  * the dense environment contraction), executed flops (padded tiles) and
  * algorithmic bytes (staged input read, FP64 output written, operator

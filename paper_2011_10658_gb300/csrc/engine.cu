@@ -197,6 +197,10 @@ void KPlan::finalize(long long k_part) {
         }
   }
   chunks.swap(nc);
+  flops = 0.0;
+  for (const KOutput& o : outs)
+    for (int c = o.chunk_begin; c < o.chunk_end; ++c)
+      if (!chunks[c].add) flops += 2.0 * o.M * o.N * chunks[c].K;
 }
 
 template <typename T>
@@ -430,6 +434,7 @@ void Engine::cached_plans(int kind, int a, int b, int n, KPlan** out, const std:
 
 int Engine::launch_plan(KPlan* pl, int fp32) {
   if (pl->tiles.empty()) return 0;
+  ops_flops_ += pl->flops;
   ensure_scratch(std::max<long long>(pl->scratch_need, 1));
   if (validate_ && !validate_plan(*pl, "plan")) return -1;
   launch_kc_gemm(pl->d_tiles, (int)pl->tiles.size(), pl->d_outs, pl->d_chunks, scratch_, stream_, fp32);
@@ -484,6 +489,14 @@ Engine::Engine(const Params& p, int chi, uint64_t seed, int precision, cudaStrea
   d_scal_ = (double*)dalloc(8192 * sizeof(double));
   d_partial_ = (double*)dalloc(304 * (kMaxKrylov + 2) * sizeof(double));
   d_err_ = (int*)dalloc(4 * sizeof(int));   // [0] tensor-core wait flag, [1] thick-restart count
+  if (!check(cudaStreamCreateWithFlags(&aux_, cudaStreamNonBlocking), "side stream")) throw std::runtime_error(err_);
+  for (int i = 0; i <= kMaxKrylov; ++i) {
+    cudaEventCreateWithFlags(&ev_iter_[i], cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&ev_conv_[i], cudaEventDisableTiming);
+  }
+  ring_dev_ = (double*)dalloc(4 * (kMaxKrylov + 1) * sizeof(double));
+  if (!check(cudaMallocHost(&ring_host_, 4 * (kMaxKrylov + 1) * sizeof(double)), "pinned ring"))
+    throw std::runtime_error(err_);
   cudaMemsetAsync(d_err_, 0, sizeof(int), stream_);
   long long dmax = 1;
   for (const Sectors& b : bonds_) dmax = std::max<long long>(dmax, b.total());
@@ -518,6 +531,15 @@ Engine::~Engine() {
   if (zpool_) cudaFree(zpool_);
   if (V_) cudaFree(V_);
   if (zb_) cudaFree(zb_);
+  if (aux_) {
+    cudaStreamSynchronize(aux_);
+    cudaStreamDestroy(aux_);
+  }
+  for (int i = 0; i <= kMaxKrylov; ++i) {
+    if (ev_iter_[i]) cudaEventDestroy(ev_iter_[i]);
+    if (ev_conv_[i]) cudaEventDestroy(ev_conv_[i]);
+  }
+  if (ring_host_) cudaFreeHost(ring_host_);
   for (void* p : allocs_) cudaFree(p);
 }
 
@@ -1297,14 +1319,20 @@ int Engine::move_path(int target) {
       leg_t = 2;
       leg_c = (nodes_[c].child_kind[0] == 1 && nodes_[c].child[0] == t) ? 0 : 1;
     }
+    cudaEvent_t e0 = nullptr;
+    if (profiling_) ev_begin(&e0);
     int rc = qr_toward(c, leg_c, move_R_);
     if (!rc) rc = absorb(t, leg_t, move_R_);
     if (rc) return rc;
+    if (profiling_) ev_end(e0, KC_MOVE_QR, 0, 0, 0);
     center_ = t;
     tc_w_node_ = -1;   // environment operators change with the move
+    if (profiling_) ev_begin(&e0);
+    ops_flops_ = 0.0;
     if (leg_c == 2) rc = compute_up(c);
     else rc = compute_down(t);
     if (rc) return rc;
+    if (profiling_) ev_end(e0, KC_MOVE_OPS, ops_flops_, ops_flops_, 0);
   }
   return check(cudaGetLastError(), "move") ? 0 : -3;
 }
@@ -2025,8 +2053,23 @@ int Engine::lanczos_run(int node, double tol, int max_krylov, bool mixed, int ma
         j0 = p;
       }
     }
+    // The convergence data of iteration j (lowest Ritz pair of T_{j+1}) is
+    // computed on a side stream and read one iteration later, so the host
+    // never waits with an empty GPU queue: iteration j+1 is already queued
+    // (speculatively) when iteration j is found converged; it only writes
+    // alpha/beta/V entries past the converged basis.
     bool done = false;
-    double host[4] = {0, 0, 0, 0};
+    int pending = -1;
+    // no speculation in the FP64 check of a mixed state: it usually ends
+    // after one product, and a speculative one would be a wasted FP64 product
+    const bool speculate = mixed || precision_ == PREC_FP64;
+    auto converged = [&](int slot) {
+      const double* h = ring_host_ + 4 * slot;
+      theta = h[0];
+      res = h[1];
+      const bool breakdown = h[2] <= 1e-13 * std::max(1.0, std::fabs(theta));
+      return res <= tol * std::max(1e-300, std::fabs(theta)) || breakdown;
+    };
     for (int j = j0; j < kmax; ++j) {
       double* vj = V_ + j * ld;
       int rc = apply_heff(vj, y_out_, -1);
@@ -2045,18 +2088,31 @@ int Engine::lanczos_run(int node, double tol, int max_krylov, bool mixed, int ma
       launch_multiaxpy(V_, ld, j + 1, coef, y_out_, n, stream_, nrm_mid, nrm_pre, kReorthRatio);
       launch_dot(y_out_, y_out_, n, d_partial_, nrm2, stream_);
       launch_sqrt(nrm2, beta + j, stream_);
-      k = j + 1;
-      launch_tridiag_lowest(alpha, beta, k, outv, svec, 0, stream_);
-      cudaMemcpyAsync(host, outv, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream_);
-      cudaMemcpyAsync(host + 2, beta + j, sizeof(double), cudaMemcpyDeviceToHost, stream_);
-      if (!check(cudaStreamSynchronize(stream_), "lanczos")) return -3;
-      const double bj = host[2];
-      theta = host[0];
-      res = host[1];
-      const bool breakdown = bj <= 1e-13 * std::max(1.0, std::fabs(theta));
-      if (res <= tol * std::max(1e-300, std::fabs(theta)) || breakdown) { done = true; break; }
+      cudaEventRecord(ev_iter_[j], stream_);
+      cudaStreamWaitEvent(aux_, ev_iter_[j], 0);
+      launch_tridiag_lowest(alpha, beta, j + 1, ring_dev_ + 4 * j, svec, 0, aux_);
+      cudaMemcpyAsync(ring_host_ + 4 * j, ring_dev_ + 4 * j, 2 * sizeof(double), cudaMemcpyDeviceToHost, aux_);
+      cudaMemcpyAsync(ring_host_ + 4 * j + 2, beta + j, sizeof(double), cudaMemcpyDeviceToHost, aux_);
+      cudaEventRecord(ev_conv_[j], aux_);
+      last_conv_ = j;
       // next Lanczos vector (column kmax holds the residual vector of a full cycle)
       launch_scale_inv_sqrt(y_out_, V_ + (j + 1) * ld, n, nrm2, stream_);
+      k = j + 1;
+      if (!speculate) {
+        if (!check(cudaEventSynchronize(ev_conv_[j]), "lanczos")) return -3;
+        if (converged(j)) { done = true; break; }
+        continue;
+      }
+      if (pending >= 0) {
+        if (!check(cudaEventSynchronize(ev_conv_[pending]), "lanczos")) return -3;
+        if (converged(pending)) { k = pending + 1; done = true; break; }
+      }
+      pending = j;
+    }
+    if (!done && pending >= 0) {
+      if (!check(cudaEventSynchronize(ev_conv_[pending]), "lanczos")) return -3;
+      k = pending + 1;
+      done = converged(pending);
     }
     if (done) break;
     // a low-precision operator stops improving at its rounding level: two
@@ -2079,6 +2135,9 @@ int Engine::lanczos_run(int node, double tol, int max_krylov, bool mixed, int ma
   double fin[2] = {theta, res};
   cudaMemcpyAsync(fin, outv, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream_);
   if (!check(cudaStreamSynchronize(stream_), "lanczos end")) return -3;
+  // a speculative iteration's convergence data may still be in flight
+  if (last_conv_ >= 0 && !check(cudaEventSynchronize(ev_conv_[last_conv_]), "lanczos end")) return -3;
+  last_conv_ = -1;
   *energy = fin[0];
   *resid = fin[1];
   *iters = total_iters;

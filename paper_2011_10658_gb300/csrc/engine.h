@@ -56,6 +56,7 @@ struct KPlan {
   std::vector<KTile> tiles;
   std::vector<int> red;
   long long scratch_need = 0;
+  double flops = 0.0;   // 2 M N K over the GEMM chunks (set by finalize)
   KChunk* d_chunks = nullptr;
   KOutput* d_outs = nullptr;
   KTile* d_tiles = nullptr;
@@ -63,7 +64,7 @@ struct KPlan {
   size_t cap_chunks = 0, cap_outs = 0, cap_tiles = 0, cap_red = 0;
   void clear() {
     chunks.clear(); outs.clear(); out_chunks.clear(); out_index.clear(); current = -1;
-    tiles.clear(); red.clear(); scratch_need = 0;
+    tiles.clear(); red.clear(); scratch_need = 0; flops = 0.0;
   }
   int add_output(double* C, long long c_m, long long c_n, int M, int N, int accumulate);
   void add_chunk(const KChunk& c);
@@ -140,7 +141,10 @@ struct TcPlan {
 // KC_MOVE and KC_LANCZOS time whole phases (centre moves with QR and
 // operator updates; Lanczos calls including their products).
 enum KernelClass {
-  KC_TC_HEFF = 0, KC_HEFF_SIMT_BOTTOM = 1, KC_HEFF_SIMT_UPPER = 2, KC_MOVE = 3, KC_LANCZOS = 4, KC_COUNT = 5
+  KC_TC_HEFF = 0, KC_HEFF_SIMT_BOTTOM = 1, KC_HEFF_SIMT_UPPER = 2, KC_MOVE = 3, KC_LANCZOS = 4,
+  KC_MOVE_QR = 5,    // per bond: QR of the departing tensor and R absorption (FP64)
+  KC_MOVE_OPS = 6,   // per bond: renormalized / environment operator update (FP64)
+  KC_COUNT = 7
 };
 struct KernelTiming {
   double ms = 0.0;
@@ -263,6 +267,7 @@ class Engine {
   std::map<std::tuple<int, int, int, int>, std::unique_ptr<KPlan>> plan_cache_;
   KPlan* cached_plan(int kind, int a, int b, int c, const std::function<void(KPlan&)>& build);
   int launch_plan(KPlan* pl, int fp32 = 0);
+  double ops_flops_ = 0.0;   // flops of the plans launched since the last reset (profiling)
   void clear_plan_caches();
   // three-stage plans (Z stages of upper nodes, then the output stage)
   void cached_plans(int kind, int a, int b, int n, KPlan** out, const std::function<void(KPlan**)>& build);
@@ -319,6 +324,13 @@ class Engine {
   // Lanczos workspace
   double* V_ = nullptr;
   double* zb_ = nullptr;        // rotated Ritz vectors of a thick restart
+  // side stream for the per-iteration tridiagonal solve and its readback
+  cudaStream_t aux_ = nullptr;
+  cudaEvent_t ev_iter_[129] = {};
+  cudaEvent_t ev_conv_[129] = {};
+  double* ring_dev_ = nullptr;    // 4 doubles per iteration: theta, residual
+  double* ring_host_ = nullptr;   // pinned copy: theta, residual, beta
+  int last_conv_ = -1;
   long long zb_elems_ = 0;
   int kmax_alloc_ = 0;
   double* d_scal_ = nullptr;   // alpha[128], beta[128], s[128], out[8], coeffs[128], partials
