@@ -99,11 +99,9 @@ int KPlan::add_output(double* C, long long c_m, long long c_n, int M, int N, int
 
 void KPlan::add_chunk(const KChunk& c) { out_chunks[current].push_back(c); }
 
-// Tiles of 32 x 32 per output.  Outputs with few tiles and long K are split
-// into parts (sub-ranges of K, chunks cut where needed) whose partial sums
-// go to scratch and are reduced in a fixed order afterwards.
-void KPlan::finalize(long long k_part) {
-  // flatten the per-output chunk lists (idempotent if already flat)
+// Flatten the per-output chunk lists into the master arrays.  Tiles are cut
+// per tile shape on first use (KPlan::variant).
+void KPlan::finalize(long long kp) {
   if (!out_chunks.empty()) {
     chunks.clear();
     for (size_t oi = 0; oi < outs.size(); ++oi) {
@@ -114,56 +112,75 @@ void KPlan::finalize(long long k_part) {
     out_chunks.clear();
     out_index.clear();
   }
-  std::vector<KChunk> nc;
-  nc.reserve(chunks.size());
-  tiles.clear();
-  red.clear();
-  scratch_need = 0;
+  k_part = kp;
+  flops = 0.0;
+  for (const KOutput& o : outs)
+    for (int c = o.chunk_begin; c < o.chunk_end; ++c)
+      if (!chunks[c].add) flops += 2.0 * o.M * o.N * chunks[c].K;
+  for (KVariant& v : var) v.ready = false;
+}
+
+// Tiles of BM x BM (BM = 16, 32 or 64) per output.  Outputs with few tiles
+// and long K are split into parts (sub-ranges of K, chunks cut where needed)
+// whose partial sums go to scratch and are reduced in a fixed order
+// afterwards.
+KVariant& KPlan::variant(int shape, cudaStream_t s) {
+  KVariant& v = var[shape];
+  if (v.ready) return v;
+  const int BMs = kc_shape_dim(shape);
+  v.tiles.clear();
+  v.red.clear();
+  v.chunks.clear();
+  v.chunks.reserve(chunks.size());
+  v.outs = outs;
+  v.scratch_need = 0;
   // K per part: small enough that the launch has about four tiles per SM
   // when the plan has few, long contractions (a Gram matrix), at most k_part
   long long work = 0, base_tiles = 0;
   for (const KOutput& o : outs) {
     long long ktot = 0;
     for (int c = o.chunk_begin; c < o.chunk_end; ++c) ktot += chunks[c].add ? 1 : chunks[c].K;
-    const long long t = (long long)((o.M + KT_BM - 1) / KT_BM) * ((o.N + KT_BN - 1) / KT_BN);
+    const long long t = (long long)((o.M + BMs - 1) / BMs) * ((o.N + BMs - 1) / BMs);
     work += t * ktot;
     base_tiles += t;
   }
-  k_part = std::max(256LL, std::min(k_part, work / (4 * 152)));
+  const long long kp = std::max(256LL, std::min(k_part, work / (4 * 152)));
   const bool few_tiles = base_tiles < 4 * 152;
+  std::vector<KChunk>& nc = v.chunks;
   for (size_t oi = 0; oi < outs.size(); ++oi) {
-    KOutput& o = outs[oi];
-    const int tm = (o.M + KT_BM - 1) / KT_BM, tn = (o.N + KT_BN - 1) / KT_BN;
+    KOutput& o = v.outs[oi];
+    const KOutput& mo = outs[oi];
+    const int tm = (o.M + BMs - 1) / BMs, tn = (o.N + BMs - 1) / BMs;
     long long ktot = 0;
-    for (int c = o.chunk_begin; c < o.chunk_end; ++c) ktot += chunks[c].add ? 1 : chunks[c].K;
-    const bool split = ktot > 2 * k_part && (tm * tn <= 16 || few_tiles);
+    for (int c = mo.chunk_begin; c < mo.chunk_end; ++c) ktot += chunks[c].add ? 1 : chunks[c].K;
+    const bool split = ktot > 2 * kp && (tm * tn <= 16 || few_tiles);
     std::vector<std::pair<int, int>> parts;   // ranges in nc
     const int begin = (int)nc.size();
     if (!split) {
-      for (int c = o.chunk_begin; c < o.chunk_end; ++c) nc.push_back(chunks[c]);
+      for (int c = mo.chunk_begin; c < mo.chunk_end; ++c) nc.push_back(chunks[c]);
       parts.push_back({begin, (int)nc.size()});
     } else {
       long long acc = 0;
       int part_begin = begin;
-      for (int c = o.chunk_begin; c < o.chunk_end; ++c) {
+      for (int c = mo.chunk_begin; c < mo.chunk_end; ++c) {
         const KChunk& ch = chunks[c];
         if (ch.add) {
           nc.push_back(ch);
           acc += 1;
         } else {
-          for (int k0 = 0; k0 < ch.K; k0 += (int)k_part) {
-            KChunk s = ch;
-            s.K = std::min<int>((int)k_part, ch.K - k0);
+          for (int k0 = 0; k0 < ch.K; k0 += (int)kp) {
+            KChunk sc = ch;
+            sc.K = std::min<int>((int)kp, ch.K - k0);
             if (ch.bmap) {
-              s.bmap = ch.bmap + k0;
-              if (ch.bval) s.bval = ch.bval + k0;
+              sc.bmap = ch.bmap + k0;
+              if (ch.bval) sc.bval = ch.bval + k0;
             } else {
-              s.B = ch.B + (long long)k0 * ch.b_k;
+              sc.B = ch.B + (long long)k0 * ch.b_k;
             }
-            s.A = ch.A + (long long)k0 * ch.a_k;
-            nc.push_back(s);
-            acc += s.K;
-            if (acc >= k_part) {
+            sc.A = ch.A + (long long)k0 * ch.a_k;
+            nc.push_back(sc);
+            acc += sc.K;
+            if (acc >= kp) {
               parts.push_back({part_begin, (int)nc.size()});
               part_begin = (int)nc.size();
               acc = 0;
@@ -177,9 +194,9 @@ void KPlan::finalize(long long k_part) {
     o.chunk_end = (int)nc.size();
     if (parts.size() > 1) {
       o.n_parts = (int)parts.size();
-      o.part_off = scratch_need;
-      scratch_need += (long long)o.n_parts * o.M * o.N;
-      red.push_back((int)oi);
+      o.part_off = v.scratch_need;
+      v.scratch_need += (long long)o.n_parts * o.M * o.N;
+      v.red.push_back((int)oi);
     } else {
       o.n_parts = 1;
     }
@@ -188,19 +205,17 @@ void KPlan::finalize(long long k_part) {
         for (int j = 0; j < tn; ++j) {
           KTile t;
           t.out = (int)oi;
-          t.m0 = i * KT_BM;
-          t.n0 = j * KT_BN;
+          t.m0 = i * BMs;
+          t.n0 = j * BMs;
           t.chunk_begin = parts[pi].first;
           t.chunk_end = parts[pi].second;
           t.part = parts.size() > 1 ? (int)pi : -1;
-          tiles.push_back(t);
+          v.tiles.push_back(t);
         }
   }
-  chunks.swap(nc);
-  flops = 0.0;
-  for (const KOutput& o : outs)
-    for (int c = o.chunk_begin; c < o.chunk_end; ++c)
-      if (!chunks[c].add) flops += 2.0 * o.M * o.N * chunks[c].K;
+  v.upload(s);
+  v.ready = true;
+  return v;
 }
 
 template <typename T>
@@ -214,14 +229,14 @@ static void grow_upload(T*& dptr, size_t& cap, const std::vector<T>& host, cudaS
   cudaMemcpyAsync(dptr, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice, s);
 }
 
-void KPlan::upload(cudaStream_t s) {
+void KVariant::upload(cudaStream_t s) {
   grow_upload(d_chunks, cap_chunks, chunks, s);
   grow_upload(d_outs, cap_outs, outs, s);
   grow_upload(d_tiles, cap_tiles, tiles, s);
   grow_upload(d_red, cap_red, red, s);
 }
 
-void KPlan::release() {
+void KVariant::release() {
   if (d_chunks) cudaFree(d_chunks);
   if (d_outs) cudaFree(d_outs);
   if (d_tiles) cudaFree(d_tiles);
@@ -231,6 +246,15 @@ void KPlan::release() {
   d_tiles = nullptr;
   d_red = nullptr;
   cap_chunks = cap_outs = cap_tiles = cap_red = 0;
+  ready = false;
+}
+
+void KPlan::release() {
+  for (KVariant& v : var) v.release();
+  for (auto& m : tev)
+    for (auto& sh : m)
+      for (cudaEvent_t& e : sh)
+        if (e) { cudaEventDestroy(e); e = nullptr; }
 }
 
 void TcPlan::release() {
@@ -342,7 +366,7 @@ bool Engine::in_range(const void* p, long long lo_bytes, long long hi_bytes) con
 // Host-side check that every chunk and output of a plan stays inside a
 // known device allocation (enabled by QED_VALIDATE=1).  Row-mapped operands
 // are checked over their whole source sector by the row-map builder.
-bool Engine::validate_plan(const KPlan& pl, const char* what) {
+bool Engine::validate_plan(const KPlan& pl, const KVariant& v, const char* what) {
   for (const KOutput& o : pl.outs) {
     const long long hi = (long long)(o.M - 1) * o.c_m + (long long)(o.N - 1) * o.c_n;
     if (o.M <= 0 || o.N <= 0 || !in_range(o.C, 0, hi * 8 + 8)) {
@@ -377,13 +401,13 @@ bool Engine::validate_plan(const KPlan& pl, const char* what) {
       }
     }
   }
-  for (const KTile& t : pl.tiles) {
-    if (t.out < 0 || t.out >= (int)pl.outs.size() || t.chunk_begin < 0 || t.chunk_end > (int)pl.chunks.size()) {
+  for (const KTile& t : v.tiles) {
+    if (t.out < 0 || t.out >= (int)v.outs.size() || t.chunk_begin < 0 || t.chunk_end > (int)v.chunks.size()) {
       err_ = std::string(what) + ": bad tile";
       return false;
     }
-    if (t.part >= 0 && !in_range(scratch_, pl.outs[t.out].part_off * 8,
-                                 (pl.outs[t.out].part_off + (long long)(t.part + 1) * pl.outs[t.out].M * pl.outs[t.out].N) * 8)) {
+    if (t.part >= 0 && !in_range(scratch_, v.outs[t.out].part_off * 8,
+                                 (v.outs[t.out].part_off + (long long)(t.part + 1) * v.outs[t.out].M * v.outs[t.out].N) * 8)) {
       err_ = std::string(what) + ": scratch out of range";
       return false;
     }
@@ -393,11 +417,56 @@ bool Engine::validate_plan(const KPlan& pl, const char* what) {
 
 int Engine::run_plan(KPlan& pl) {
   pl.finalize(kKPart);
-  ensure_scratch(std::max<long long>(pl.scratch_need, 1));
-  if (validate_ && !validate_plan(pl, "plan")) return -1;
-  pl.upload(stream_);
-  launch_kc_gemm(pl.d_tiles, (int)pl.tiles.size(), pl.d_outs, pl.d_chunks, scratch_, stream_);
-  launch_kc_reduce(pl.d_outs, (int)pl.outs.size(), pl.d_red, (int)pl.red.size(), scratch_, stream_);
+  return launch_kplan(pl, 0, false);
+}
+
+// Launch a plan with a tile shape.  Tuned plans (cached, replayed) try every
+// shape once, timed with CUDA events, after one untimed launch, then keep the
+// fastest per arithmetic (FP64 / FP32); every launch computes the full
+// result.  QED_KC_SHAPE=16|32|64 forces one shape.
+int Engine::launch_kplan(KPlan& pl, int fp32, bool tune) {
+  if (pl.outs.empty()) return 0;
+  const int mode = fp32 ? 1 : 0;
+  int shape = forced_shape_ >= 0 ? forced_shape_ : (tune ? pl.shape[mode] : (int)KS_32);
+  int timed = -1;
+  if (shape < 0) {
+    const int t = pl.trials[mode];
+    if (t == 0) {
+      shape = KS_32;
+    } else if (t <= KS_COUNT) {
+      shape = t - 1;
+      timed = shape;
+    } else {
+      float best = 1e30f;
+      int bs = KS_32;
+      for (int sh = 0; sh < KS_COUNT; ++sh) {
+        cudaEvent_t* e = pl.tev[mode][sh];
+        float ms = 0.0f;
+        if (e[0] && e[1] && cudaEventSynchronize(e[1]) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, e[0], e[1]) == cudaSuccess && ms < best) {
+          best = ms;
+          bs = sh;
+        }
+        for (int i = 0; i < 2; ++i)
+          if (e[i]) { cudaEventDestroy(e[i]); e[i] = nullptr; }
+      }
+      pl.shape[mode] = bs;
+      shape = bs;
+    }
+    pl.trials[mode] = t + 1;
+  }
+  KVariant& v = pl.variant(shape, stream_);
+  ensure_scratch(std::max<long long>(v.scratch_need, 1));
+  if (validate_ && !validate_plan(pl, v, "plan")) return -1;
+  if (timed >= 0) {
+    cudaEvent_t* e = pl.tev[mode][timed];
+    for (int i = 0; i < 2; ++i)
+      if (!e[i]) cudaEventCreate(&e[i]);
+    cudaEventRecord(e[0], stream_);
+  }
+  launch_kc_gemm(v.d_tiles, (int)v.tiles.size(), v.d_outs, v.d_chunks, scratch_, stream_, fp32, shape);
+  launch_kc_reduce(v.d_outs, (int)v.outs.size(), v.d_red, (int)v.red.size(), scratch_, stream_);
+  if (timed >= 0) cudaEventRecord(pl.tev[mode][timed][1], stream_);
   return check(cudaGetLastError(), "kc_gemm launch") ? 0 : -3;
 }
 
@@ -408,7 +477,6 @@ KPlan* Engine::cached_plan(int kind, int a, int b, int c, const std::function<vo
   std::unique_ptr<KPlan> pl(new KPlan);
   build(*pl);
   pl->finalize(kKPart);
-  pl->upload(stream_);
   KPlan* raw = pl.get();
   plan_cache_[key] = std::move(pl);
   return raw;
@@ -425,7 +493,6 @@ void Engine::cached_plans(int kind, int a, int b, int n, KPlan** out, const std:
     build(raw);
     for (int i = 0; i < n; ++i) {
       raw[i]->finalize(kKPart);
-      raw[i]->upload(stream_);
       plan_cache_[std::make_tuple(kind, a, b, i)] = std::move(pl[i]);
     }
   }
@@ -433,13 +500,8 @@ void Engine::cached_plans(int kind, int a, int b, int n, KPlan** out, const std:
 }
 
 int Engine::launch_plan(KPlan* pl, int fp32) {
-  if (pl->tiles.empty()) return 0;
   ops_flops_ += pl->flops;
-  ensure_scratch(std::max<long long>(pl->scratch_need, 1));
-  if (validate_ && !validate_plan(*pl, "plan")) return -1;
-  launch_kc_gemm(pl->d_tiles, (int)pl->tiles.size(), pl->d_outs, pl->d_chunks, scratch_, stream_, fp32);
-  launch_kc_reduce(pl->d_outs, (int)pl->outs.size(), pl->d_red, (int)pl->red.size(), scratch_, stream_);
-  return check(cudaGetLastError(), "kc_gemm launch") ? 0 : -3;
+  return launch_kplan(*pl, fp32, true);
 }
 
 void Engine::clear_plan_caches() {
@@ -459,6 +521,10 @@ Engine::Engine(const Params& p, int chi, uint64_t seed, int precision, cudaStrea
   lat_ = Lattice{p.Lx, p.Ly, p.Lz};
   const char* v = std::getenv("QED_VALIDATE");
   validate_ = v && v[0] == '1';
+  if (const char* ks = std::getenv("QED_KC_SHAPE")) {
+    const int d = std::atoi(ks);
+    forced_shape_ = d == 16 ? KS_16 : (d == 32 ? KS_32 : (d == 64 ? KS_64 : -1));
+  }
   build_terms(p, &terms_, &constant_);
   nodes_ = build_tree(p.Lx, p.Ly, p.Lz);
   std::string err;
@@ -1593,16 +1659,7 @@ Engine::HeffPlans* Engine::heff_plans(int node, int cls, bool adjoint) {
     for (int i = 0; i < 2; ++i) st[i].finalize(kKPart);
   }
   s3.finalize(kKPart);
-  for (int i = 0; i < 3; ++i) {
-    hp->scratch_need = std::max(hp->scratch_need, st[i].scratch_need);
-    st[i].upload(stream_);
-    for (const KOutput& o : st[i].outs)
-      for (int c = o.chunk_begin; c < o.chunk_end; ++c)
-        if (!st[i].chunks[c].add) hp->flops += 2.0 * o.M * o.N * st[i].chunks[c].K;
-  }
-  if (validate_)
-    for (int i = 0; i < 3; ++i)
-      if (!validate_plan(st[i], "H_eff plan")) return nullptr;
+  for (int i = 0; i < 3; ++i) hp->flops += st[i].flops;
   if (!check(cudaGetLastError(), "plan")) return nullptr;
   HeffPlans* raw = hp.get();
   heff_cache_[key] = std::move(hp);
@@ -1626,7 +1683,6 @@ int Engine::apply_heff(const double* x, double* y, int cls) {
   }
   HeffPlans* hp = heff_plans(center_, cls, false);
   if (!hp) return -1;
-  ensure_scratch(std::max<long long>(hp->scratch_need, 1));
   if (x != x_in_) launch_copy(x, x_in_, n, stream_);
   cudaEvent_t e0 = nullptr;
   if (profiling_) ev_begin(&e0);
@@ -1636,10 +1692,8 @@ int Engine::apply_heff(const double* x, double* y, int cls) {
   }
   const int fp32 = (use_mixed_ && cls < 0) ? 1 : 0;
   for (int i = 0; i < 3; ++i) {
-    KPlan& pl = hp->st[i];
-    if (pl.tiles.empty()) continue;
-    launch_kc_gemm(pl.d_tiles, (int)pl.tiles.size(), pl.d_outs, pl.d_chunks, scratch_, stream_, fp32);
-    launch_kc_reduce(pl.d_outs, (int)pl.outs.size(), pl.d_red, (int)pl.red.size(), scratch_, stream_);
+    const int rc = launch_kplan(hp->st[i], fp32, true);
+    if (rc) return rc;
   }
   if (profiling_) ev_end(e0, bottom ? KC_HEFF_SIMT_BOTTOM : KC_HEFF_SIMT_UPPER, hp->flops, hp->flops, 0.0);
   if (y != y_out_) launch_copy(y_out_, y, n, stream_);
@@ -1654,14 +1708,11 @@ int Engine::apply_heff_adjoint(const double* x, double* y) {
   const bool bottom = nodes_[center_].child_kind[0] == 0;
   HeffPlans* hp = heff_plans(center_, -1, true);
   if (!hp) return -1;
-  ensure_scratch(std::max<long long>(hp->scratch_need, 1));
   if (x != x_in_) launch_copy(x, x_in_, n, stream_);
   if (!bottom && hp->z_elems > 0) cudaMemsetAsync(zpool_, 0, hp->z_elems * sizeof(double), stream_);
   for (int i = 0; i < 3; ++i) {
-    KPlan& pl = hp->st[i];
-    if (pl.tiles.empty()) continue;
-    launch_kc_gemm(pl.d_tiles, (int)pl.tiles.size(), pl.d_outs, pl.d_chunks, scratch_, stream_, 0);
-    launch_kc_reduce(pl.d_outs, (int)pl.outs.size(), pl.d_red, (int)pl.red.size(), scratch_, stream_);
+    const int rc = launch_kplan(hp->st[i], 0, true);
+    if (rc) return rc;
   }
   if (y != y_out_) launch_copy(y_out_, y, n, stream_);
   return check(cudaGetLastError(), "apply_heff_adjoint") ? 0 : -3;

@@ -47,29 +47,48 @@ struct Layout {
 // Outputs that name the same destination (pointer and shape) are merged, so
 // every output region is written by exactly one output: contributions to a
 // shared block are K-concatenated chunks, never concurrent writes.
+// One tile-shape cut of a plan: tiles, chunks split into K parts where
+// needed, outputs with their partial-sum slots, reduction list.
+struct KVariant {
+  std::vector<KTile> tiles;
+  std::vector<KChunk> chunks;
+  std::vector<KOutput> outs;
+  std::vector<int> red;
+  long long scratch_need = 0;
+  KChunk* d_chunks = nullptr;
+  KOutput* d_outs = nullptr;
+  KTile* d_tiles = nullptr;
+  int* d_red = nullptr;
+  size_t cap_chunks = 0, cap_outs = 0, cap_tiles = 0, cap_red = 0;
+  bool ready = false;
+  void upload(cudaStream_t s);
+  void release();
+  ~KVariant() { release(); }
+};
+
+// Grouped-GEMM work list: outputs, each with its chunks (built through
+// add_output / add_chunk, flattened by finalize), cut into tiles per tile
+// shape on demand, with the chosen shape per arithmetic (FP64, FP32).
 struct KPlan {
   std::vector<KChunk> chunks;
   std::vector<KOutput> outs;
   std::vector<std::vector<KChunk>> out_chunks;
   std::map<std::tuple<uintptr_t, long long, long long, int, int>, int> out_index;
   int current = -1;
-  std::vector<KTile> tiles;
-  std::vector<int> red;
-  long long scratch_need = 0;
+  long long k_part = 4096;
   double flops = 0.0;   // 2 M N K over the GEMM chunks (set by finalize)
-  KChunk* d_chunks = nullptr;
-  KOutput* d_outs = nullptr;
-  KTile* d_tiles = nullptr;
-  int* d_red = nullptr;
-  size_t cap_chunks = 0, cap_outs = 0, cap_tiles = 0, cap_red = 0;
+  KVariant var[KS_COUNT];
+  int shape[2] = {-1, -1};    // tuned tile shape per arithmetic, -1 while tuning
+  int trials[2] = {0, 0};
+  cudaEvent_t tev[2][KS_COUNT][2] = {};
   void clear() {
-    chunks.clear(); outs.clear(); out_chunks.clear(); out_index.clear(); current = -1;
-    tiles.clear(); red.clear(); scratch_need = 0; flops = 0.0;
+    chunks.clear(); outs.clear(); out_chunks.clear(); out_index.clear(); current = -1; flops = 0.0;
+    for (KVariant& v : var) v.ready = false;
   }
   int add_output(double* C, long long c_m, long long c_n, int M, int N, int accumulate);
   void add_chunk(const KChunk& c);
   void finalize(long long k_part);
-  void upload(cudaStream_t s);
+  KVariant& variant(int shape, cudaStream_t s);
   void release();
   ~KPlan() { release(); }
 };
@@ -267,6 +286,8 @@ class Engine {
   std::map<std::tuple<int, int, int, int>, std::unique_ptr<KPlan>> plan_cache_;
   KPlan* cached_plan(int kind, int a, int b, int c, const std::function<void(KPlan&)>& build);
   int launch_plan(KPlan* pl, int fp32 = 0);
+  int launch_kplan(KPlan& pl, int fp32, bool tune);
+  int forced_shape_ = -1;   // QED_KC_SHAPE
   double ops_flops_ = 0.0;   // flops of the plans launched since the last reset (profiling)
   void clear_plan_caches();
   // three-stage plans (Z stages of upper nodes, then the output stage)
@@ -274,7 +295,6 @@ class Engine {
   struct HeffPlans {
     KPlan st[3];
     long long z_elems = 0;       // Z pool prefix the stages use
-    long long scratch_need = 0;  // split-K scratch
     double flops = 0.0;          // algorithmic flops of one product
   };
   std::map<std::pair<int, int>, std::unique_ptr<HeffPlans>> heff_cache_;
@@ -340,7 +360,7 @@ class Engine {
   // device allocations (base, bytes) for the optional plan validator
   std::map<uintptr_t, size_t> ranges_;
   bool validate_ = false;
-  bool validate_plan(const KPlan& pl, const char* what);
+  bool validate_plan(const KPlan& pl, const KVariant& v, const char* what);
   void track(void* p, size_t bytes) { if (p) ranges_[(uintptr_t)p] = bytes; }
   void untrack(void* p) { ranges_.erase((uintptr_t)p); }
   bool in_range(const void* p, long long lo_off, long long hi_off) const;

@@ -39,7 +39,7 @@ struct KOutput {
   long long part_off; // scratch offset (doubles) of this output's partials
 };
 
-// One CTA's work: a 32x32 tile of an output over a chunk range.
+// One CTA's work: a BM x BN tile of an output over a chunk range.
 struct KTile {
   int out;
   int m0, n0;
@@ -47,13 +47,17 @@ struct KTile {
   int part;           // partial slot (-1: write C directly)
 };
 
-constexpr int KT_BM = 32;
+constexpr int KT_BM = 32;   // tile of the default shape
 constexpr int KT_BN = 32;
+// Tile shapes of the grouped GEMM: square tiles of 16, 32 or 64.
+enum KcShape { KS_16 = 0, KS_32 = 1, KS_64 = 2, KS_COUNT = 3 };
+inline int kc_shape_dim(int shape) { return 16 << shape; }
 
 // fp32 != 0: same contraction with FP32 multiply-accumulate (operands
-// rounded to FP32 on load, results stored as FP64).
+// rounded to FP32 on load, results stored as FP64).  shape: the tile shape
+// the tiles were cut with.
 void launch_kc_gemm(const KTile* tiles, int n_tiles, const KOutput* outs, const KChunk* chunks,
-                    double* scratch, cudaStream_t s, int fp32 = 0);
+                    double* scratch, cudaStream_t s, int fp32 = 0, int shape = KS_32);
 void launch_kc_reduce(const KOutput* outs, int n_outs, const int* red_list, int n_red, double* scratch,
                       cudaStream_t s);
 

@@ -47,58 +47,70 @@ __device__ __forceinline__ double load_b(const KChunk& c, int k, int n) {
   return scale * c.B[row * c.b_k + (long long)n * c.b_n];
 }
 
-template <typename T>
+// One CTA computes a BM x BN tile of one output (16 x 16 threads, each a
+// BM/16 x BN/16 register tile) over its chunk range, K staged in slabs of 16.
+template <typename T, int BM, int BN>
 __global__ void __launch_bounds__(THREADS) kc_gemm_kernel(const KTile* __restrict__ tiles,
                                                            const KOutput* __restrict__ outs,
                                                            const KChunk* __restrict__ chunks,
                                                            double* __restrict__ scratch) {
-  __shared__ T As[BK][KT_BM + 1];
-  __shared__ T Bs[BK][KT_BN + 1];
+  constexpr int TM = BM / 16, TN = BN / 16;
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
   const KTile tile = tiles[blockIdx.x];
   const KOutput out = outs[tile.out];
   const int tid = threadIdx.x;
-  // each thread owns a 2x2 micro tile: rows ty*2.., cols tx*2..
   const int tx = tid % 16, ty = tid / 16;
-  T acc[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
+  T acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
   for (int ci = tile.chunk_begin; ci < tile.chunk_end; ++ci) {
     const KChunk c = chunks[ci];
     if (c.add) {
       // C[m,n] += alpha * A[m,n]
-      for (int i = 0; i < 2; ++i)
-        for (int j = 0; j < 2; ++j) {
-          int m = tile.m0 + ty * 2 + i, n = tile.n0 + tx * 2 + j;
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+          const int m = tile.m0 + ty * TM + i, n = tile.n0 + tx * TN + j;
           if (m < out.M && n < out.N) acc[i][j] += (T)(c.alpha * load_a(c, m, n));
         }
       continue;
     }
     for (int k0 = 0; k0 < c.K; k0 += BK) {
-      // load A tile (32 x 16) and B tile (16 x 32): 512 elements each, 2 per thread
-      for (int e = tid; e < KT_BM * BK; e += THREADS) {
-        int mm = e / BK, kk = e % BK;
-        int m = tile.m0 + mm, k = k0 + kk;
+      for (int e = tid; e < BM * BK; e += THREADS) {
+        const int mm = e / BK, kk = e % BK;
+        const int m = tile.m0 + mm, k = k0 + kk;
         As[kk][mm] = (m < out.M && k < c.K) ? (T)(c.alpha * load_a(c, m, k)) : T(0);
       }
-      for (int e = tid; e < KT_BN * BK; e += THREADS) {
-        int kk = e / KT_BN, nn = e % KT_BN;
-        int n = tile.n0 + nn, k = k0 + kk;
+      for (int e = tid; e < BN * BK; e += THREADS) {
+        const int kk = e / BN, nn = e % BN;
+        const int n = tile.n0 + nn, k = k0 + kk;
         Bs[kk][nn] = (n < out.N && k < c.K) ? (T)load_b(c, k, n) : T(0);
       }
       __syncthreads();
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
-        T a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
-        T b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
-        acc[0][0] = fma(a0, b0, acc[0][0]);
-        acc[0][1] = fma(a0, b1, acc[0][1]);
-        acc[1][0] = fma(a1, b0, acc[1][0]);
-        acc[1][1] = fma(a1, b1, acc[1][1]);
+        T a[TM], bv[TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) bv[j] = Bs[kk][tx * TN + j];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
       }
       __syncthreads();
     }
   }
-  for (int i = 0; i < 2; ++i)
-    for (int j = 0; j < 2; ++j) {
-      int m = tile.m0 + ty * 2 + i, n = tile.n0 + tx * 2 + j;
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int m = tile.m0 + ty * TM + i, n = tile.n0 + tx * TN + j;
       if (m >= out.M || n >= out.N) continue;
       if (tile.part >= 0) {
         scratch[out.part_off + (long long)tile.part * out.M * out.N + (long long)m * out.N + n] = (double)acc[i][j];
@@ -717,12 +729,19 @@ int grid_for(long long n) {
 }  // namespace
 
 void launch_kc_gemm(const KTile* tiles, int n_tiles, const KOutput* outs, const KChunk* chunks, double* scratch,
-                    cudaStream_t s, int fp32) {
+                    cudaStream_t s, int fp32, int shape) {
   if (n_tiles <= 0) return;
-  if (fp32)
-    kc_gemm_kernel<float><<<n_tiles, THREADS, 0, s>>>(tiles, outs, chunks, scratch);
-  else
-    kc_gemm_kernel<double><<<n_tiles, THREADS, 0, s>>>(tiles, outs, chunks, scratch);
+#define QED_KC(T, B) kc_gemm_kernel<T, B, B><<<n_tiles, THREADS, 0, s>>>(tiles, outs, chunks, scratch)
+  if (fp32) {
+    if (shape == KS_16) QED_KC(float, 16);
+    else if (shape == KS_64) QED_KC(float, 64);
+    else QED_KC(float, 32);
+  } else {
+    if (shape == KS_16) QED_KC(double, 16);
+    else if (shape == KS_64) QED_KC(double, 64);
+    else QED_KC(double, 32);
+  }
+#undef QED_KC
   count_launches(1);
 }
 

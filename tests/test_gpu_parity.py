@@ -138,3 +138,23 @@ def test_energy_classes_and_observables(pair):
     np.testing.assert_allclose(s.measure("phi"), obs["phi"], atol=1e-9)
     np.testing.assert_allclose(s.measure("elink"), obs["E_link"], atol=1e-9)
     np.testing.assert_allclose(s.measure("sigma"), obs["sigma"], atol=1e-9)
+
+
+@pytest.mark.parametrize("shape", ["16", "32", "64"])
+def test_every_tile_shape_matches_oracle(q, shape, monkeypatch):
+    """The grouped GEMM's tile shapes (forced with QED_KC_SHAPE; normally
+    picked per plan by timing) give the oracle's products and node updates."""
+    monkeypatch.setenv("QED_KC_SHAPE", shape)
+    p, ref, m, s = make_pair(q, (2, 2, 1), 12, 3, t=0.8, m=0.3, ge2=1.5, cB=0.9, nu=20.0, Q=1)
+    rng = np.random.default_rng(21)
+    for target in range(len(ref.nodes)):
+        ref.move_to(target)
+        s.move_center(target)
+        x = rng.standard_normal(s.node_size(target))
+        y = s.apply_heff(x)
+        X = from_layout(x, ref.labels[target], ref.T[target].shape)
+        assert max_rel(y, to_layout(ref.heff_apply(target, X), ref.labels[target])) < 1e-11
+    for idx in range(len(ref.nodes)):
+        e_ref = ref.optimize_node(idx, tol=1e-12)
+        e = s.optimize_node(idx, tol=1e-12, max_krylov=64)
+        assert abs(e - e_ref) < REL_FP64 * abs(e_ref)
