@@ -152,6 +152,20 @@ int ttn_sweep(ttn_state *s, int32_t n_sweeps, double tol, int32_t max_krylov, tt
  * vector with FP64 products until the FP64 residual reaches tol.  Default
  * mixed_tol: 1e-7 (TF32X3), 1e-5 (TF32), 1e-4 (BF16). */
 int ttn_set_mixed_tol(ttn_state *s, double mixed_tol);
+/* n_sweeps sweeps of n independent problems together (batching of
+ * independent ground-state problems, e.g. several charge sectors and
+ * couplings).  The states must share the lattice size, the precision and
+ * the CUDA stream; sector tables, couplings and seeds may differ.  The
+ * problems update each node together: per-problem centre moves, then a
+ * lockstep Lanczos (same algorithm as ttn_sweep) whose H_eff products for
+ * all problems are one grouped launch (the tensor-core tiles or grouped-GEMM
+ * chunks of every problem), replayed from a CUDA graph once the grouped
+ * GEMM's tile shape is tuned (no graph on the legacy default stream); the
+ * FP64 check of a mixed-precision update runs per problem.  out: n entries
+ * (seconds = wall time of the whole call).  QED_ENOCONV if some update of
+ * some problem stopped above tolerance (stats valid). */
+int ttn_batch_sweep(ttn_state *const *states, int32_t n, int32_t n_sweeps, double tol, int32_t max_krylov,
+                    ttn_sweep_stats *out);
 /* Switch the product precision of an existing state (QED_PREC_*); resets
  * mixed_tol to its default for that precision. */
 int ttn_set_precision(ttn_state *s, int precision);

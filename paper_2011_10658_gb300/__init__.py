@@ -45,6 +45,18 @@ def local_op(parity, kind, j1=0, j2=0):
     return src, val
 
 
+def batch_sweep(states, n=1, tol=1e-12, max_krylov=64, allow_noconv=False):
+    """n sweeps of several independent TTN states together (ttn_batch_sweep);
+    one stats dict per state."""
+    k = len(states)
+    handles = (ctypes.c_void_p * k)(*[st._h.value for st in states])
+    stats = (SweepStats * k)()
+    check(lib().ttn_batch_sweep(handles, k, n, tol, max_krylov, stats), allow=(-4,) if allow_noconv else ())
+    return [dict(energy=st.energy, matvecs=st.matvecs, matvecs_mixed=st.matvecs_mixed,
+                 node_updates=st.node_updates, not_converged=st.not_converged,
+                 max_rel_residual=st.max_rel_residual, seconds=st.seconds) for st in stats]
+
+
 class Model:
     """Lattice, term list and tree (qed_model_create)."""
 

@@ -48,6 +48,8 @@ SIGNATURES = [
     ("ttn_create", c_int, [c_void_p, c_int32, ctypes.c_uint64, c_int, c_void_p, ctypes.POINTER(c_void_p)]),
     ("ttn_destroy", None, [c_void_p]),
     ("ttn_sweep", c_int, [c_void_p, c_int32, c_double, c_int32, ctypes.POINTER(SweepStats)]),
+    ("ttn_batch_sweep", c_int, [ctypes.POINTER(c_void_p), c_int32, c_int32, c_double, c_int32,
+                                 ctypes.POINTER(SweepStats)]),
     ("ttn_optimize_node", c_int, [c_void_p, c_int32, c_double, c_int32, c_double_p]),
     ("ttn_set_mixed_tol", c_int, [c_void_p, c_double]),
     ("ttn_set_precision", c_int, [c_void_p, c_int]),

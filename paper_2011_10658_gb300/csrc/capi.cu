@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/qedttn.h"
+#include "batch.h"
 #include "engine.h"
 #include "model.h"
 #include "state.h"
@@ -288,6 +289,54 @@ QED_API int ttn_kernel_timing(ttn_state* s, int kernel_class, double* ms, int64_
     if (flops_alg) *flops_alg = k.flops_alg;
     if (flops_exec) *flops_exec = k.flops_exec;
     if (bytes_alg) *bytes_alg = k.bytes_alg;
+    return QED_OK;)
+}
+
+QED_API int ttn_batch_sweep(ttn_state* const* states, int32_t n, int32_t n_sweeps, double tol, int32_t max_krylov,
+                            ttn_sweep_stats* out) {
+  if (!states || n < 1) return fail(QED_EINVAL, "need at least one state");
+  if (n_sweeps < 0 || !(tol > 0.0) || max_krylov < 2 || max_krylov > 128)
+    return fail(QED_EINVAL, "n_sweeps >= 0, tol > 0, 2 <= max_krylov <= 128");
+  std::vector<qed::Engine*> es;
+  for (int i = 0; i < n; ++i) {
+    if (!states[i]) return fail(QED_EINVAL, "null state");
+    const qed::Params& a = states[0]->model->p;
+    const qed::Params& b = states[i]->model->p;
+    if (a.Lx != b.Lx || a.Ly != b.Ly || a.Lz != b.Lz) return fail(QED_EINVAL, "states differ in lattice size");
+    if (states[i]->engine->precision() != states[0]->engine->precision())
+      return fail(QED_EINVAL, "states differ in precision");
+    if (states[i]->engine->stream() != states[0]->engine->stream()) return fail(QED_EINVAL, "states differ in stream");
+    for (int j = 0; j < i; ++j)
+      if (states[j] == states[i]) return fail(QED_EINVAL, "a state appears twice");
+    es.push_back(states[i]->engine);
+  }
+  QED_TRY(
+    auto t0 = std::chrono::steady_clock::now();
+    std::vector<qed::SweepStats> st(n);
+    qed::BatchRunner runner(es);
+    for (int i = 0; i < n_sweeps; ++i) {
+      int rc = runner.sweep(tol, max_krylov, &st);
+      if (rc) {
+        for (qed::Engine* e : es)
+          if (!e->error().empty()) return engine_status(e, rc);
+        return engine_status(es[0], rc);
+      }
+    }
+    auto t1 = std::chrono::steady_clock::now();
+    int bad = 0;
+    for (int i = 0; i < n; ++i) {
+      if (out) {
+        out[i].energy = st[i].energy;
+        out[i].matvecs = st[i].matvecs;
+        out[i].matvecs_mixed = st[i].matvecs_mixed;
+        out[i].node_updates = st[i].node_updates;
+        out[i].not_converged = st[i].not_converged;
+        out[i].max_rel_residual = st[i].max_residual;
+        out[i].seconds = std::chrono::duration<double>(t1 - t0).count();
+      }
+      bad += st[i].not_converged;
+    }
+    if (bad) return fail(QED_ENOCONV, "some node updates stopped above tolerance");
     return QED_OK;)
 }
 

@@ -21,9 +21,8 @@ namespace qed {
 
 namespace {
 constexpr long long kKPart = 4096;     // split-K granularity for tall contractions
-constexpr int kMaxKrylov = 128;
-constexpr double kReorthRatio = 0.5;
-constexpr int kThickKeep = 8;          // Ritz vectors kept by a thick restart   // second Gram-Schmidt pass if ||w||^2 dropped below half
+constexpr double kReorthRatio = 0.5;   // second Gram-Schmidt pass if ||w||^2 dropped below half
+constexpr int kThickKeep = 8;          // Ritz vectors kept by a thick restart
 // Centre-move QR rank handling: a sector whose QR diagonal falls below
 // kQrFallback x (largest column norm) is factorised by Gram-Schmidt, where a
 // remainder below kQrDependent x (largest column norm) marks a dependent
@@ -354,6 +353,13 @@ void Engine::ensure_zpool(long long elems) {
 
 // [p + lo_bytes, p + hi_bytes) inside one tracked allocation?
 bool Engine::in_range(const void* p, long long lo_bytes, long long hi_bytes) const {
+  if (in_own_range(p, lo_bytes, hi_bytes)) return true;
+  for (const Engine* e : peers_)
+    if (e != this && e->in_own_range(p, lo_bytes, hi_bytes)) return true;
+  return false;
+}
+
+bool Engine::in_own_range(const void* p, long long lo_bytes, long long hi_bytes) const {
   const uintptr_t a = (uintptr_t)p;
   auto it = ranges_.upper_bound(a + (lo_bytes < 0 ? 0 : 0));
   if (it == ranges_.begin()) return false;
@@ -506,6 +512,7 @@ int Engine::launch_plan(KPlan* pl, int fp32) {
 
 void Engine::clear_plan_caches() {
   cudaStreamSynchronize(stream_);
+  ++gen_;
   plan_cache_.clear();
   heff_cache_.clear();
 }
@@ -1944,13 +1951,15 @@ TcPlan* Engine::tc_plan(int node) {
 
 void Engine::clear_tc_cache() {
   cudaStreamSynchronize(stream_);
+  ++gen_;
   tc_cache_.clear();
   tc_w_node_ = -1;
 }
 
-int Engine::apply_heff_mixed() {
+// Tensor-core plan of the centre with its environment blocks staged.
+TcPlan* Engine::tc_prepare() {
   TcPlan* tc = tc_plan(center_);
-  if (!tc) return -1;
+  if (!tc) return nullptr;
   const int elem = precision_ == PREC_BF16 ? 2 : 4;
   const int split = precision_ == PREC_TF32X3 ? 1 : 0;
   if (tc_w_node_ != center_) {
@@ -1959,6 +1968,14 @@ int Engine::apply_heff_mixed() {
     launch_convert(elem, split ? 2 : 0, tc->d_wjobs, (int)tc->wjobs.size(), tc->w_max_elems, stream_);
     tc_w_node_ = center_;
   }
+  return tc;
+}
+
+int Engine::apply_heff_mixed() {
+  TcPlan* tc = tc_prepare();
+  if (!tc) return -1;
+  const int elem = precision_ == PREC_BF16 ? 2 : 4;
+  const int split = precision_ == PREC_TF32X3 ? 1 : 0;
   launch_convert(elem, split, tc->d_xjobs, (int)tc->xjobs.size(), tc->x_max_elems, stream_);
   cudaEvent_t e0 = nullptr;
   if (profiling_) ev_begin(&e0);
@@ -2041,28 +2058,21 @@ int Engine::lanczos(int node, double tol, int max_krylov, bool mixed, int max_re
   return rc;
 }
 
-int Engine::lanczos_run(int node, double tol, int max_krylov, bool mixed, int max_restarts, double* energy,
-                        double* resid, int* iters) {
-  use_mixed_ = mixed;
-  const long long n = layout_[node].size;
-  int kmax = std::min(std::max(max_krylov, 2), kMaxKrylov);
-  if (kmax > n) kmax = (int)n;
+// ---- Lanczos building blocks (shared by the single-state and the batched
+// drivers).  Scalars live in d_scal_: alpha[128], beta[128], s[128], out,
+// Gram-Schmidt coefficients, norms; a thick restart's k x keep combination.
+namespace {
+constexpr int kAlpha = 0, kBeta = 128, kSvec = 256, kOut = 384, kCoef = 512, kNrm2 = 640, kNrmPre = 641,
+              kNrmMid = 642, kCmat = 1024;
+}
+
+int Engine::lz_prepare(int kmax) {
   if (kmax_alloc_ < kmax + 1) {
     if (V_) { untrack(V_); cudaFree(V_); }
     if (!check(cudaMalloc(&V_, (size_t)(kmax + 1) * nmax_ * sizeof(double)), "Krylov basis")) return -2;
     track(V_, (size_t)(kmax + 1) * nmax_ * sizeof(double));
     kmax_alloc_ = kmax + 1;
   }
-  double* alpha = d_scal_;
-  double* beta = d_scal_ + 128;
-  double* svec = d_scal_ + 256;
-  double* outv = d_scal_ + 384;
-  double* coef = d_scal_ + 512;
-  double* nrm2 = d_scal_ + 640;
-  double* nrm_pre = d_scal_ + 641;
-  double* nrm_mid = d_scal_ + 642;
-  double* xvec = tmp_;
-  const long long ld = nmax_;
   const int keep = std::min(kThickKeep, kmax / 4);
   if (keep >= 1 && zb_elems_ < (long long)keep * nmax_) {
     if (zb_) { untrack(zb_); cudaFree(zb_); }
@@ -2070,100 +2080,155 @@ int Engine::lanczos_run(int node, double tol, int max_krylov, bool mixed, int ma
     if (!check(cudaMalloc(&zb_, zb_elems_ * sizeof(double)), "restart basis")) return -2;
     track(zb_, zb_elems_ * sizeof(double));
   }
-  double* Cmat = d_scal_ + 1024;   // k x keep combination of a thick restart
-  launch_copy(T_[node], xvec, n, stream_);
-  launch_dot(xvec, xvec, n, d_partial_, nrm2, stream_);
-  launch_scale_inv_sqrt(xvec, V_, n, nrm2, stream_);
+  return 0;
+}
+
+// v_0 = T[node] / |T[node]|
+void Engine::lz_start(int node) {
+  const long long n = layout_[node].size;
+  launch_copy(T_[node], tmp_, n, stream_);
+  launch_dot(tmp_, tmp_, n, d_partial_, d_scal_ + kNrm2, stream_);
+  launch_scale_inv_sqrt(tmp_, V_, n, d_scal_ + kNrm2, stream_);
+}
+
+// With y_out_ = H_eff v_j: alpha_j, the three-term recurrence, full
+// reorthogonalisation (one classical Gram-Schmidt pass, a second only if the
+// first removed more than half of ||w||^2) and beta_j = ||w||.
+void Engine::lz_iteration(int j, long long n) {
+  const long long ld = nmax_;
+  double* alpha = d_scal_ + kAlpha;
+  double* beta = d_scal_ + kBeta;
+  double* coef = d_scal_ + kCoef;
+  double* vj = V_ + j * ld;
+  launch_dot(vj, y_out_, n, d_partial_, alpha + j, stream_);
+  launch_axpby(vj, y_out_, n, alpha + j, 0.0, -1.0, nullptr, 1.0, stream_);
+  if (j > 0) launch_axpby(V_ + (j - 1) * ld, y_out_, n, beta + (j - 1), 0.0, -1.0, nullptr, 1.0, stream_);
+  launch_dot(y_out_, y_out_, n, d_partial_, d_scal_ + kNrmPre, stream_);
+  launch_multidot(V_, ld, j + 1, y_out_, n, d_partial_, coef, stream_);
+  launch_multiaxpy(V_, ld, j + 1, coef, y_out_, n, stream_);
+  launch_dot(y_out_, y_out_, n, d_partial_, d_scal_ + kNrmMid, stream_);
+  launch_multidot(V_, ld, j + 1, y_out_, n, d_partial_, coef, stream_, d_scal_ + kNrmMid, d_scal_ + kNrmPre,
+                  kReorthRatio);
+  launch_multiaxpy(V_, ld, j + 1, coef, y_out_, n, stream_, d_scal_ + kNrmMid, d_scal_ + kNrmPre, kReorthRatio);
+  launch_dot(y_out_, y_out_, n, d_partial_, d_scal_ + kNrm2, stream_);
+  launch_sqrt(d_scal_ + kNrm2, beta + j, stream_);
+}
+
+// v_{j+1} = w / beta_j (column kmax holds the residual vector of a full cycle)
+void Engine::lz_next_vector(int j, long long n) {
+  launch_scale_inv_sqrt(y_out_, V_ + (long long)(j + 1) * nmax_, n, d_scal_ + kNrm2, stream_);
+}
+
+// Thick restart after a full cycle of k vectors (see lanczos_restart_kernel);
+// *j0 = vectors carried into the next cycle.  Synchronises the stream.
+int Engine::lz_thick_restart(int k, int kmax, long long n, int* j0) {
+  const long long ld = nmax_;
+  double* alpha = d_scal_ + kAlpha;
+  double* beta = d_scal_ + kBeta;
+  const int keep = std::min(kThickKeep, kmax / 4);
+  if (keep < 1) {   // explicit restart from the Ritz vector
+    launch_tridiag_lowest(alpha, beta, k, d_scal_ + kOut, d_scal_ + kSvec, 1, stream_);
+    launch_combine(V_, ld, k, d_scal_ + kSvec, tmp_, n, stream_);
+    launch_dot(tmp_, tmp_, n, d_partial_, d_scal_ + kNrm2, stream_);
+    launch_scale_inv_sqrt(tmp_, V_, n, d_scal_ + kNrm2, stream_);
+    *j0 = 0;
+    return 0;
+  }
+  launch_lanczos_restart(alpha, beta, k, keep, d_scal_ + kCmat, d_err_ + 1, stream_);
+  int p = 0;
+  cudaMemcpyAsync(&p, d_err_ + 1, sizeof(int), cudaMemcpyDeviceToHost, stream_);
+  if (!check(cudaStreamSynchronize(stream_), "thick restart")) return -3;
+  if (p < 1 || p > keep) {
+    err_ = "thick restart: invalid kept count";
+    return -3;
+  }
+  launch_rotate_basis(V_, ld, k, d_scal_ + kCmat, p, zb_, n, stream_);
+  cudaMemcpyAsync(V_, zb_, (size_t)p * ld * sizeof(double), cudaMemcpyDeviceToDevice, stream_);
+  launch_copy(V_ + (long long)kmax * ld, V_ + (long long)p * ld, n, stream_);
+  *j0 = p;
+  return 0;
+}
+
+// Ritz vector x = V s of the last k vectors, normalised into T[node]; the
+// Ritz value and residual estimate go to the final ring slot (read after a
+// synchronisation).
+void Engine::lz_finish(int node, int k) {
+  const long long n = layout_[node].size;
+  launch_tridiag_lowest(d_scal_ + kAlpha, d_scal_ + kBeta, k, d_scal_ + kOut, d_scal_ + kSvec, 1, stream_);
+  launch_combine(V_, nmax_, k, d_scal_ + kSvec, tmp_, n, stream_);
+  launch_dot(tmp_, tmp_, n, d_partial_, d_scal_ + kNrm2, stream_);
+  launch_scale_inv_sqrt(tmp_, T_[node], n, d_scal_ + kNrm2, stream_);
+  cudaMemcpyAsync(ring_host_ + 4 * kMaxKrylov, d_scal_ + kOut, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream_);
+}
+
+// Convergence data of iteration j (lowest Ritz pair of T_{j+1}, beta_j) into
+// ring slot j, computed on the side stream.
+void Engine::lz_queue_check(int j) {
+  cudaEventRecord(ev_iter_[j], stream_);
+  cudaStreamWaitEvent(aux_, ev_iter_[j], 0);
+  launch_tridiag_lowest(d_scal_ + kAlpha, d_scal_ + kBeta, j + 1, ring_dev_ + 4 * j, d_scal_ + kSvec, 0, aux_);
+  cudaMemcpyAsync(ring_host_ + 4 * j, ring_dev_ + 4 * j, 2 * sizeof(double), cudaMemcpyDeviceToHost, aux_);
+  cudaMemcpyAsync(ring_host_ + 4 * j + 2, d_scal_ + kBeta + j, sizeof(double), cudaMemcpyDeviceToHost, aux_);
+  cudaEventRecord(ev_conv_[j], aux_);
+  last_conv_ = j;
+}
+
+bool Engine::lz_converged(int slot, double tol, double* theta, double* res) const {
+  const double* h = ring_host_ + 4 * slot;
+  *theta = h[0];
+  *res = h[1];
+  const bool breakdown = h[2] <= 1e-13 * std::max(1.0, std::fabs(*theta));
+  return *res <= tol * std::max(1e-300, std::fabs(*theta)) || breakdown;
+}
+
+int Engine::lanczos_run(int node, double tol, int max_krylov, bool mixed, int max_restarts, double* energy,
+                        double* resid, int* iters) {
+  use_mixed_ = mixed;
+  const long long n = layout_[node].size;
+  int kmax = std::min(std::max(max_krylov, 2), kMaxKrylov);
+  if (kmax > n) kmax = (int)n;
+  int rc = lz_prepare(kmax);
+  if (rc) return rc;
+  lz_start(node);
   int total_iters = 0;
   double theta = 0.0, res = 0.0, prev_res = 1e300;
   int stalls = 0;
   int j0 = 0;   // vectors carried into the cycle (thick restart)
   int k = 0;
+  // no speculation in the FP64 check of a mixed state: it usually ends
+  // after one product, and a speculative one would be a wasted FP64 product
+  const bool speculate = mixed || precision_ == PREC_FP64;
   for (int restart = 0; restart < max_restarts; ++restart) {
-    if (restart > 0) {
-      // thick restart: keep the lowest Ritz vectors, continue from the
-      // residual vector stored in column kmax
-      if (keep < 1) {
-        launch_tridiag_lowest(alpha, beta, k, outv, svec, 1, stream_);
-        launch_combine(V_, ld, k, svec, xvec, n, stream_);
-        launch_dot(xvec, xvec, n, d_partial_, nrm2, stream_);
-        launch_scale_inv_sqrt(xvec, V_, n, nrm2, stream_);
-        j0 = 0;
-      } else {
-        launch_lanczos_restart(alpha, beta, k, keep, Cmat, d_err_ + 1, stream_);
-        int p = 0;
-        cudaMemcpyAsync(&p, d_err_ + 1, sizeof(int), cudaMemcpyDeviceToHost, stream_);
-        if (!check(cudaStreamSynchronize(stream_), "thick restart")) return -3;
-        if (p < 1 || p > keep) {
-          err_ = "thick restart: invalid kept count";
-          return -3;
-        }
-        launch_rotate_basis(V_, ld, k, Cmat, p, zb_, n, stream_);
-        cudaMemcpyAsync(V_, zb_, (size_t)p * ld * sizeof(double), cudaMemcpyDeviceToDevice, stream_);
-        launch_copy(V_ + (long long)kmax * ld, V_ + (long long)p * ld, n, stream_);
-        j0 = p;
-      }
-    }
-    // The convergence data of iteration j (lowest Ritz pair of T_{j+1}) is
-    // computed on a side stream and read one iteration later, so the host
-    // never waits with an empty GPU queue: iteration j+1 is already queued
-    // (speculatively) when iteration j is found converged; it only writes
-    // alpha/beta/V entries past the converged basis.
+    if (restart > 0 && (rc = lz_thick_restart(k, kmax, n, &j0))) return rc;
+    // The convergence data of iteration j is computed on a side stream and
+    // read one iteration later, so the host never waits with an empty GPU
+    // queue: iteration j+1 is already queued (speculatively) when iteration
+    // j is found converged; it only writes alpha/beta/V entries past the
+    // converged basis.
     bool done = false;
     int pending = -1;
-    // no speculation in the FP64 check of a mixed state: it usually ends
-    // after one product, and a speculative one would be a wasted FP64 product
-    const bool speculate = mixed || precision_ == PREC_FP64;
-    auto converged = [&](int slot) {
-      const double* h = ring_host_ + 4 * slot;
-      theta = h[0];
-      res = h[1];
-      const bool breakdown = h[2] <= 1e-13 * std::max(1.0, std::fabs(theta));
-      return res <= tol * std::max(1e-300, std::fabs(theta)) || breakdown;
-    };
     for (int j = j0; j < kmax; ++j) {
-      double* vj = V_ + j * ld;
-      int rc = apply_heff(vj, y_out_, -1);
-      if (rc) return rc;
+      if ((rc = apply_heff(V_ + j * nmax_, y_out_, -1))) return rc;
       ++total_iters;
-      launch_dot(vj, y_out_, n, d_partial_, alpha + j, stream_);
-      launch_axpby(vj, y_out_, n, alpha + j, 0.0, -1.0, nullptr, 1.0, stream_);
-      if (j > 0) launch_axpby(V_ + (j - 1) * ld, y_out_, n, beta + (j - 1), 0.0, -1.0, nullptr, 1.0, stream_);
-      // full reorthogonalisation: one classical Gram-Schmidt pass, and a
-      // second one only if the first removed more than half of ||w||^2
-      launch_dot(y_out_, y_out_, n, d_partial_, nrm_pre, stream_);
-      launch_multidot(V_, ld, j + 1, y_out_, n, d_partial_, coef, stream_);
-      launch_multiaxpy(V_, ld, j + 1, coef, y_out_, n, stream_);
-      launch_dot(y_out_, y_out_, n, d_partial_, nrm_mid, stream_);
-      launch_multidot(V_, ld, j + 1, y_out_, n, d_partial_, coef, stream_, nrm_mid, nrm_pre, kReorthRatio);
-      launch_multiaxpy(V_, ld, j + 1, coef, y_out_, n, stream_, nrm_mid, nrm_pre, kReorthRatio);
-      launch_dot(y_out_, y_out_, n, d_partial_, nrm2, stream_);
-      launch_sqrt(nrm2, beta + j, stream_);
-      cudaEventRecord(ev_iter_[j], stream_);
-      cudaStreamWaitEvent(aux_, ev_iter_[j], 0);
-      launch_tridiag_lowest(alpha, beta, j + 1, ring_dev_ + 4 * j, svec, 0, aux_);
-      cudaMemcpyAsync(ring_host_ + 4 * j, ring_dev_ + 4 * j, 2 * sizeof(double), cudaMemcpyDeviceToHost, aux_);
-      cudaMemcpyAsync(ring_host_ + 4 * j + 2, beta + j, sizeof(double), cudaMemcpyDeviceToHost, aux_);
-      cudaEventRecord(ev_conv_[j], aux_);
-      last_conv_ = j;
-      // next Lanczos vector (column kmax holds the residual vector of a full cycle)
-      launch_scale_inv_sqrt(y_out_, V_ + (j + 1) * ld, n, nrm2, stream_);
+      lz_iteration(j, n);
+      lz_queue_check(j);
+      lz_next_vector(j, n);
       k = j + 1;
       if (!speculate) {
         if (!check(cudaEventSynchronize(ev_conv_[j]), "lanczos")) return -3;
-        if (converged(j)) { done = true; break; }
+        if (lz_converged(j, tol, &theta, &res)) { done = true; break; }
         continue;
       }
       if (pending >= 0) {
         if (!check(cudaEventSynchronize(ev_conv_[pending]), "lanczos")) return -3;
-        if (converged(pending)) { k = pending + 1; done = true; break; }
+        if (lz_converged(pending, tol, &theta, &res)) { k = pending + 1; done = true; break; }
       }
       pending = j;
     }
     if (!done && pending >= 0) {
       if (!check(cudaEventSynchronize(ev_conv_[pending]), "lanczos")) return -3;
       k = pending + 1;
-      done = converged(pending);
+      done = lz_converged(pending, tol, &theta, &res);
     }
     if (done) break;
     // a low-precision operator stops improving at its rounding level: two
@@ -2176,21 +2241,14 @@ int Engine::lanczos_run(int node, double tol, int max_krylov, bool mixed, int ma
     }
     prev_res = std::min(prev_res, res);
   }
-  // Ritz vector x = V s of the last cycle
-  launch_tridiag_lowest(alpha, beta, k, outv, svec, 1, stream_);
-  launch_combine(V_, ld, k, svec, xvec, n, stream_);
+  lz_finish(node, k);
   use_mixed_ = false;
-  // normalise
-  launch_dot(xvec, xvec, n, d_partial_, nrm2, stream_);
-  launch_scale_inv_sqrt(xvec, T_[node], n, nrm2, stream_);
-  double fin[2] = {theta, res};
-  cudaMemcpyAsync(fin, outv, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream_);
   if (!check(cudaStreamSynchronize(stream_), "lanczos end")) return -3;
   // a speculative iteration's convergence data may still be in flight
   if (last_conv_ >= 0 && !check(cudaEventSynchronize(ev_conv_[last_conv_]), "lanczos end")) return -3;
   last_conv_ = -1;
-  *energy = fin[0];
-  *resid = fin[1];
+  *energy = ring_host_[4 * kMaxKrylov];
+  *resid = ring_host_[4 * kMaxKrylov + 1];
   *iters = total_iters;
   return 0;
 }

@@ -16,6 +16,8 @@
 
 namespace qed {
 
+constexpr int kMaxKrylov = 128;   // largest Lanczos basis
+
 enum Precision { PREC_FP64 = 0, PREC_TF32 = 1, PREC_BF16 = 2, PREC_TF32X3 = 3 };
 
 // Block layout of a three-leg tensor T[a, b, c] whose blocks (q_a, q_b)
@@ -339,6 +341,9 @@ class Engine {
   void ev_begin(cudaEvent_t* e);
   void ev_end(cudaEvent_t a, int cls, double fa, double fe, double ba);
   TcPlan* tc_plan(int node);
+  TcPlan* tc_prepare();
+  // bumped whenever cached plans are dropped (their device pointers go stale)
+  uint64_t gen_ = 0;
   int apply_heff_mixed();
   bool mixed_node(int node) const;
   // Lanczos workspace
@@ -363,7 +368,9 @@ class Engine {
   bool validate_plan(const KPlan& pl, const KVariant& v, const char* what);
   void track(void* p, size_t bytes) { if (p) ranges_[(uintptr_t)p] = bytes; }
   void untrack(void* p) { ranges_.erase((uintptr_t)p); }
-  bool in_range(const void* p, long long lo_off, long long hi_off) const;
+  bool in_range(const void* p, long long lo_off, long long hi_off) const;   // own or a peer's
+  bool in_own_range(const void* p, long long lo_off, long long hi_off) const;
+  std::vector<const Engine*> peers_;   // other engines whose allocations a grouped plan may touch
   void* dalloc(size_t bytes);
   bool check(cudaError_t e, const char* what);
   const SiteOp* site_op(int parity, const OpKey& key);
@@ -397,6 +404,16 @@ class Engine {
   int lanczos_run(int node, double tol, int max_krylov, bool mixed, int max_restarts, double* energy, double* resid,
                   int* iters);
   int move_path(int target);
+  // Lanczos building blocks
+  int lz_prepare(int kmax);
+  void lz_start(int node);
+  void lz_iteration(int j, long long n);
+  void lz_next_vector(int j, long long n);
+  int lz_thick_restart(int k, int kmax, long long n, int* j0);
+  void lz_finish(int node, int k);
+  void lz_queue_check(int j);
+  bool lz_converged(int slot, double tol, double* theta, double* res) const;
+  friend class BatchRunner;
   bool use_mixed_ = false;   // current matvec precision inside lanczos
 };
 
