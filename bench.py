@@ -343,14 +343,19 @@ def run_native(args):
     compare = None
     if args.compare_fp64 and args.precision != "fp64" and rank == 0:
         r = q.TTN(model, CHI, seed=SEED + rank, precision="fp64", stream=stream.cuda_stream)
-        e64 = []
-        t0 = time.time()
+        e64, t64 = [], []
         for _ in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            t0 = time.time()
             e64.append(r.sweep(1, tol=TOL, max_krylov=KRYLOV, allow_noconv=True)["energy"])
-        fp64_s = (time.time() - t0) / (args.warmup + args.steps)
+            torch.cuda.synchronize()
+            t64.append(time.time() - t0)
         rel = [abs(a - b) / abs(b) for a, b in zip(energies, e64)]
+        # the same sweeps as the timed mixed ones (after the warm-up sweeps)
+        fp64_timed = sum(t64[args.warmup:]) / max(1, args.steps)
         compare = {"energies_mixed": energies, "energies_fp64": e64, "max_rel_dE": max(rel),
-                   "fp64_seconds_per_sweep": fp64_s}
+                   "fp64_seconds_per_sweep_each": t64, "fp64_seconds_per_timed_sweep": fp64_timed,
+                   "speedup_same_sweeps": fp64_timed / (elapsed_ms / args.steps / 1e3)}
         r.close()
 
     cpu = None
@@ -405,6 +410,59 @@ def run_heff_only(args):
     s.close()
 
 
+def batch_problems(n):
+    """Independent problems of the batching workload (4x4x4, chi = 48): problem
+    i has charge q = 2 (i mod 9), g^2 = (0.5, 2)[(i // 9) mod 2], m = (0.5, 1)[(i // 18)
+    mod 2], seed (2 << 32) + i."""
+    out = []
+    for i in range(n):
+        g2 = (0.5, 2.0)[(i // 9) % 2]
+        mass = (0.5, 1.0)[(i // 18) % 2]
+        c = workloads.qed_couplings(g2, t=1.0, m=mass)
+        out.append((dict(c, Q=2 * (i % 9)), (2 << 32) + i))
+    return out
+
+
+def run_batch(args):
+    """Batched sweeps (one grouped product launch per lockstep Lanczos step,
+    CUDA graphs) against the same problems swept one after another."""
+    import torch
+    import paper_2011_10658_gb300 as q
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    probs = batch_problems(args.problems)
+
+    def make():
+        return [q.TTN(q.Model(4, 4, 4, **kw), 48, seed=seed, precision=args.precision, stream=stream.cuda_stream)
+                for kw, seed in probs]
+
+    seq, bat = make(), make()
+    for s in seq:
+        s.sweep(1, tol=TOL, max_krylov=KRYLOV, allow_noconv=True)
+    q.batch_sweep(bat, 1, tol=TOL, max_krylov=KRYLOV, allow_noconv=True)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    e_seq = [s.sweep(args.steps, tol=TOL, max_krylov=KRYLOV, allow_noconv=True)["energy"] for s in seq]
+    torch.cuda.synchronize()
+    t_seq = time.time() - t0
+    l0 = q.launch_count()
+    t0 = time.time()
+    st = q.batch_sweep(bat, args.steps, tol=TOL, max_krylov=KRYLOV, allow_noconv=True)
+    torch.cuda.synchronize()
+    t_bat = time.time() - t0
+    launches = q.launch_count() - l0
+    e_bat = [x["energy"] for x in st]
+    rel = max(abs(a - b) / abs(b) for a, b in zip(e_bat, e_seq))
+    units = args.problems * args.steps
+    print(json.dumps({
+        "metric": "batched TTN sweeps (problem-sweeps/s)", "value": units / t_bat, "unit": "problem-sweeps/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": 1, "higher_is_better": True, "dtype": args.precision,
+        "data": "synthetic", "config": {"workload": f"{args.problems} independent 4x4x4 chi=48 problems "
+                                                    "(q = 0..16, g^2 in {0.5, 2}, m in {0.5, 1})"},
+        "sequential_value": units / t_seq, "speedup_vs_sequential": t_seq / t_bat,
+        "max_rel_dE_batch_vs_sequential": rel, "gpu_launches": launches}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -416,8 +474,10 @@ def main():
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--mode", default="sweep", choices=["sweep", "heff"],
-                    help="heff: only H_eff x products at --node (profiling aid)")
+    ap.add_argument("--mode", default="sweep", choices=["sweep", "heff", "batch"],
+                    help="heff: only H_eff x products at --node (profiling aid); batch: batched "
+                         "independent problems against sequential sweeps")
+    ap.add_argument("--problems", type=int, default=8, help="batch mode: number of problems")
     ap.add_argument("--node", type=int, default=0)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -426,6 +486,8 @@ def main():
         run_reference(args)
     elif args.mode == "heff":
         run_heff_only(args)
+    elif args.mode == "batch":
+        run_batch(args)
     else:
         run_native(args)
 
