@@ -252,8 +252,9 @@ void KPlan::release() {
   for (KVariant& v : var) v.release();
   for (auto& m : tev)
     for (auto& sh : m)
-      for (cudaEvent_t& e : sh)
-        if (e) { cudaEventDestroy(e); e = nullptr; }
+      for (auto& rep : sh)
+        for (cudaEvent_t& e : rep)
+          if (e) { cudaEventDestroy(e); e = nullptr; }
 }
 
 void TcPlan::release() {
@@ -426,53 +427,92 @@ int Engine::run_plan(KPlan& pl) {
   return launch_kplan(pl, 0, false);
 }
 
-// Launch a plan with a tile shape.  Tuned plans (cached, replayed) try every
-// shape once, timed with CUDA events, after one untimed launch, then keep the
-// fastest per arithmetic (FP64 / FP32); every launch computes the full
-// result.  QED_KC_SHAPE=16|32|64 forces one shape.
+// Multiply-adds a tile shape executes, padding included (split parts ignored).
+double KPlan::padded_work(int shape) const {
+  const double B = kc_shape_dim(shape);
+  double w = 0.0;
+  for (const KOutput& o : outs) {
+    double k = 0.0;
+    for (int c = o.chunk_begin; c < o.chunk_end; ++c) k += chunks[c].add ? 1.0 : chunks[c].K;
+    w += std::ceil(o.M / B) * std::ceil(o.N / B) * B * B * k;
+  }
+  return w;
+}
+
+// Tile shapes worth timing: those whose padded work is within 1.5x of the
+// least, least padded first.
+int KPlan::candidates(int* out) const {
+  double w[KS_COUNT], best = 1e300;
+  for (int sh = 0; sh < KS_COUNT; ++sh) best = std::min(best, w[sh] = padded_work(sh));
+  int n = 0;
+  for (int sh = 0; sh < KS_COUNT; ++sh)
+    if (w[sh] <= 1.5 * best) out[n++] = sh;
+  std::sort(out, out + n, [&](int x, int y) { return w[x] < w[y]; });
+  return n;
+}
+
+// Launch a plan with a tile shape.  Tuned plans (cached, replayed) are the
+// autotuner's subjects: after one untimed launch with the least padded
+// shape, every candidate shape (padded work within 1.5x of the least) is
+// launched twice under CUDA events, interleaved, and the plan keeps the shape
+// with the shortest of its two times, per arithmetic (FP64 / FP32).  Every
+// launch computes the full result.  QED_KC_SHAPE=16|32|64 forces one shape.
 int Engine::launch_kplan(KPlan& pl, int fp32, bool tune) {
   if (pl.outs.empty()) return 0;
   const int mode = fp32 ? 1 : 0;
-  int shape = forced_shape_ >= 0 ? forced_shape_ : (tune ? pl.shape[mode] : (int)KS_32);
-  int timed = -1;
+  int shape = forced_shape_ >= 0 ? forced_shape_ : pl.shape[mode];
+  if (shape < 0 && !tune) {   // one-off plans: the least padded shape
+    int cand[KS_COUNT];
+    pl.candidates(cand);
+    shape = cand[0];
+  }
+  cudaEvent_t* timed = nullptr;
   if (shape < 0) {
+    int cand[KS_COUNT];
+    const int nc = pl.candidates(cand);
     const int t = pl.trials[mode];
-    if (t == 0) {
-      shape = KS_32;
-    } else if (t <= KS_COUNT) {
-      shape = t - 1;
-      timed = shape;
+    if (nc == 1) {
+      pl.shape[mode] = shape = cand[0];
+    } else if (t == 0) {
+      shape = cand[0];
+    } else if (t <= 2 * nc) {
+      const int idx = (t - 1) % nc, rep = (t - 1) / nc;
+      shape = cand[idx];
+      timed = pl.tev[mode][shape][rep];
     } else {
       float best = 1e30f;
-      int bs = KS_32;
-      for (int sh = 0; sh < KS_COUNT; ++sh) {
-        cudaEvent_t* e = pl.tev[mode][sh];
-        float ms = 0.0f;
-        if (e[0] && e[1] && cudaEventSynchronize(e[1]) == cudaSuccess &&
-            cudaEventElapsedTime(&ms, e[0], e[1]) == cudaSuccess && ms < best) {
-          best = ms;
-          bs = sh;
+      int bs = cand[0];
+      for (int i = 0; i < nc; ++i) {
+        const int sh = cand[i];
+        for (int rep = 0; rep < 2; ++rep) {
+          cudaEvent_t* e = pl.tev[mode][sh][rep];
+          float ms = 0.0f;
+          if (e[0] && e[1] && cudaEventSynchronize(e[1]) == cudaSuccess &&
+              cudaEventElapsedTime(&ms, e[0], e[1]) == cudaSuccess && ms < best) {
+            best = ms;
+            bs = sh;
+          }
         }
-        for (int i = 0; i < 2; ++i)
-          if (e[i]) { cudaEventDestroy(e[i]); e[i] = nullptr; }
       }
-      pl.shape[mode] = bs;
-      shape = bs;
+      for (auto& sh : pl.tev[mode])
+        for (auto& rep : sh)
+          for (cudaEvent_t& e : rep)
+            if (e) { cudaEventDestroy(e); e = nullptr; }
+      pl.shape[mode] = shape = bs;
     }
     pl.trials[mode] = t + 1;
   }
   KVariant& v = pl.variant(shape, stream_);
   ensure_scratch(std::max<long long>(v.scratch_need, 1));
   if (validate_ && !validate_plan(pl, v, "plan")) return -1;
-  if (timed >= 0) {
-    cudaEvent_t* e = pl.tev[mode][timed];
+  if (timed) {
     for (int i = 0; i < 2; ++i)
-      if (!e[i]) cudaEventCreate(&e[i]);
-    cudaEventRecord(e[0], stream_);
+      if (!timed[i]) cudaEventCreate(&timed[i]);
+    cudaEventRecord(timed[0], stream_);
   }
   launch_kc_gemm(v.d_tiles, (int)v.tiles.size(), v.d_outs, v.d_chunks, scratch_, stream_, fp32, shape);
   launch_kc_reduce(v.d_outs, (int)v.outs.size(), v.d_red, (int)v.red.size(), scratch_, stream_);
-  if (timed >= 0) cudaEventRecord(pl.tev[mode][timed][1], stream_);
+  if (timed) cudaEventRecord(timed[1], stream_);
   return check(cudaGetLastError(), "kc_gemm launch") ? 0 : -3;
 }
 

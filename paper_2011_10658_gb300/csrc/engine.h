@@ -82,7 +82,7 @@ struct KPlan {
   KVariant var[KS_COUNT];
   int shape[2] = {-1, -1};    // tuned tile shape per arithmetic, -1 while tuning
   int trials[2] = {0, 0};
-  cudaEvent_t tev[2][KS_COUNT][2] = {};
+  cudaEvent_t tev[2][KS_COUNT][2][2] = {};   // [arithmetic][shape][repeat][start, stop]
   void clear() {
     chunks.clear(); outs.clear(); out_chunks.clear(); out_index.clear(); current = -1; flops = 0.0;
     for (KVariant& v : var) v.ready = false;
@@ -91,6 +91,8 @@ struct KPlan {
   void add_chunk(const KChunk& c);
   void finalize(long long k_part);
   KVariant& variant(int shape, cudaStream_t s);
+  double padded_work(int shape) const;
+  int candidates(int* out) const;
   void release();
   ~KPlan() { release(); }
 };
