@@ -126,7 +126,7 @@ void KPlan::finalize(long long kp) {
 KVariant& KPlan::variant(int shape, cudaStream_t s) {
   KVariant& v = var[shape];
   if (v.ready) return v;
-  const int BMs = kc_shape_dim(shape);
+  const int BMs = kc_shape_m(shape), BNs = kc_shape_n(shape);
   v.tiles.clear();
   v.red.clear();
   v.chunks.clear();
@@ -139,7 +139,7 @@ KVariant& KPlan::variant(int shape, cudaStream_t s) {
   for (const KOutput& o : outs) {
     long long ktot = 0;
     for (int c = o.chunk_begin; c < o.chunk_end; ++c) ktot += chunks[c].add ? 1 : chunks[c].K;
-    const long long t = (long long)((o.M + BMs - 1) / BMs) * ((o.N + BMs - 1) / BMs);
+    const long long t = (long long)((o.M + BMs - 1) / BMs) * ((o.N + BNs - 1) / BNs);
     work += t * ktot;
     base_tiles += t;
   }
@@ -149,7 +149,7 @@ KVariant& KPlan::variant(int shape, cudaStream_t s) {
   for (size_t oi = 0; oi < outs.size(); ++oi) {
     KOutput& o = v.outs[oi];
     const KOutput& mo = outs[oi];
-    const int tm = (o.M + BMs - 1) / BMs, tn = (o.N + BMs - 1) / BMs;
+    const int tm = (o.M + BMs - 1) / BMs, tn = (o.N + BNs - 1) / BNs;
     long long ktot = 0;
     for (int c = mo.chunk_begin; c < mo.chunk_end; ++c) ktot += chunks[c].add ? 1 : chunks[c].K;
     const bool split = ktot > 2 * kp && (tm * tn <= 16 || few_tiles);
@@ -205,7 +205,7 @@ KVariant& KPlan::variant(int shape, cudaStream_t s) {
           KTile t;
           t.out = (int)oi;
           t.m0 = i * BMs;
-          t.n0 = j * BMs;
+          t.n0 = j * BNs;
           t.chunk_begin = parts[pi].first;
           t.chunk_end = parts[pi].second;
           t.part = parts.size() > 1 ? (int)pi : -1;
@@ -429,12 +429,12 @@ int Engine::run_plan(KPlan& pl) {
 
 // Multiply-adds a tile shape executes, padding included (split parts ignored).
 double KPlan::padded_work(int shape) const {
-  const double B = kc_shape_dim(shape);
+  const double BM = kc_shape_m(shape), BN = kc_shape_n(shape);
   double w = 0.0;
   for (const KOutput& o : outs) {
     double k = 0.0;
     for (int c = o.chunk_begin; c < o.chunk_end; ++c) k += chunks[c].add ? 1.0 : chunks[c].K;
-    w += std::ceil(o.M / B) * std::ceil(o.N / B) * B * B * k;
+    w += std::ceil(o.M / BM) * std::ceil(o.N / BN) * BM * BN * k;
   }
   return w;
 }
@@ -456,7 +456,8 @@ int KPlan::candidates(int* out) const {
 // shape, every candidate shape (padded work within 1.5x of the least) is
 // launched twice under CUDA events, interleaved, and the plan keeps the shape
 // with the shortest of its two times, per arithmetic (FP64 / FP32).  Every
-// launch computes the full result.  QED_KC_SHAPE=16|32|64 forces one shape.
+// launch computes the full result.  QED_KC_SHAPE=16|32|64|1664|6416 forces one shape
+// (the last two: 16x64 and 64x16).
 int Engine::launch_kplan(KPlan& pl, int fp32, bool tune) {
   if (pl.outs.empty()) return 0;
   const int mode = fp32 ? 1 : 0;
@@ -570,7 +571,7 @@ Engine::Engine(const Params& p, int chi, uint64_t seed, int precision, cudaStrea
   validate_ = v && v[0] == '1';
   if (const char* ks = std::getenv("QED_KC_SHAPE")) {
     const int d = std::atoi(ks);
-    forced_shape_ = d == 16 ? KS_16 : (d == 32 ? KS_32 : (d == 64 ? KS_64 : -1));
+    forced_shape_ = d == 16 ? KS_16 : (d == 32 ? KS_32 : (d == 64 ? KS_64 : (d == 1664 ? KS_16x64 : (d == 6416 ? KS_64x16 : -1))));
   }
   build_terms(p, &terms_, &constant_);
   nodes_ = build_tree(p.Lx, p.Ly, p.Lz);

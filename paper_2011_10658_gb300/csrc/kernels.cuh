@@ -49,9 +49,18 @@ struct KTile {
 
 constexpr int KT_BM = 32;   // tile of the default shape
 constexpr int KT_BN = 32;
-// Tile shapes of the grouped GEMM: square tiles of 16, 32 or 64.
-enum KcShape { KS_16 = 0, KS_32 = 1, KS_64 = 2, KS_COUNT = 3 };
-inline int kc_shape_dim(int shape) { return 16 << shape; }
+// Tile shapes of the grouped GEMM (rows x columns of the output tile):
+// 16x16, 32x32, 64x64, and the flat 16x64 / 64x16 for outputs with few rows
+// (leg operators applied to a node tensor) or few columns.
+enum KcShape { KS_16 = 0, KS_32 = 1, KS_64 = 2, KS_16x64 = 3, KS_64x16 = 4, KS_COUNT = 5 };
+inline int kc_shape_m(int shape) {
+  static const int m[KS_COUNT] = {16, 32, 64, 16, 64};
+  return m[shape];
+}
+inline int kc_shape_n(int shape) {
+  static const int n[KS_COUNT] = {16, 32, 64, 64, 16};
+  return n[shape];
+}
 
 // fp32 != 0: same contraction with FP32 multiply-accumulate (operands
 // rounded to FP32 on load, results stored as FP64).  shape: the tile shape

@@ -731,16 +731,21 @@ int grid_for(long long n) {
 void launch_kc_gemm(const KTile* tiles, int n_tiles, const KOutput* outs, const KChunk* chunks, double* scratch,
                     cudaStream_t s, int fp32, int shape) {
   if (n_tiles <= 0) return;
-#define QED_KC(T, B) kc_gemm_kernel<T, B, B><<<n_tiles, THREADS, 0, s>>>(tiles, outs, chunks, scratch)
-  if (fp32) {
-    if (shape == KS_16) QED_KC(float, 16);
-    else if (shape == KS_64) QED_KC(float, 64);
-    else QED_KC(float, 32);
-  } else {
-    if (shape == KS_16) QED_KC(double, 16);
-    else if (shape == KS_64) QED_KC(double, 64);
-    else QED_KC(double, 32);
+#define QED_KC(T, BM, BN) kc_gemm_kernel<T, BM, BN><<<n_tiles, THREADS, 0, s>>>(tiles, outs, chunks, scratch)
+#define QED_KC_ALL(T)                       \
+  switch (shape) {                          \
+    case KS_16: QED_KC(T, 16, 16); break;   \
+    case KS_64: QED_KC(T, 64, 64); break;   \
+    case KS_16x64: QED_KC(T, 16, 64); break; \
+    case KS_64x16: QED_KC(T, 64, 16); break; \
+    default: QED_KC(T, 32, 32); break;      \
   }
+  if (fp32) {
+    QED_KC_ALL(float)
+  } else {
+    QED_KC_ALL(double)
+  }
+#undef QED_KC_ALL
 #undef QED_KC
   count_launches(1);
 }

@@ -140,7 +140,7 @@ def test_energy_classes_and_observables(pair):
     np.testing.assert_allclose(s.measure("sigma"), obs["sigma"], atol=1e-9)
 
 
-@pytest.mark.parametrize("shape", ["16", "32", "64"])
+@pytest.mark.parametrize("shape", ["16", "32", "64", "1664", "6416"])
 def test_every_tile_shape_matches_oracle(q, shape, monkeypatch):
     """The grouped GEMM's tile shapes (forced with QED_KC_SHAPE; normally
     picked per plan by timing) give the oracle's products and node updates."""
