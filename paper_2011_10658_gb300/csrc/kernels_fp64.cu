@@ -20,31 +20,81 @@ namespace {
 constexpr int BK = 16;
 constexpr int THREADS = 256;
 
-// Row maps are sign-encoded: -1 = zero row, otherwise (row << 1) | negate.
-__device__ __forceinline__ double load_a(const KChunk& c, int m, int k) {
-  long long row = m;
-  double scale = 1.0;
-  if (c.amap) {
-    int r = c.amap[m];
-    if (r < 0) return 0.0;
-    row = r >> 1;
-    if (r & 1) scale = -1.0;
-  }
-  if (c.aval) scale *= c.aval[m];
-  return scale * c.A[row * c.a_m + (long long)k * c.a_k];
+// FP64 -> FP32 with round-to-nearest-even, done on the integer pipes from the
+// IEEE-754 formats (sign, rebiased exponent, top 23 of the 52 fraction bits,
+// rounding on the 29 dropped bits; a carry out of the fraction bumps the
+// exponent, up to infinity).  Magnitudes below the FP32 normal range become
+// signed zero, NaN stays NaN.  GB300 runs FP64 instructions, conversions
+// included, at a small fraction of its FP32 rate, so the FP32 grouped GEMM
+// converts its FP64 operands this way.
+__device__ __forceinline__ float d2f_bits(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ff);
+  const unsigned long long frac = b & 0xFFFFFFFFFFFFFull;
+  if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (frac ? 0x400000u : 0u));
+  const int fe = e - 1023 + 127;
+  if (fe <= 0) return __uint_as_float(sign);
+  if (fe >= 255) return __uint_as_float(sign | 0x7f800000u);
+  unsigned r = sign | ((unsigned)fe << 23) | (unsigned)(frac >> 29);
+  const unsigned rem = (unsigned)(frac & 0x1FFFFFFFull);
+  if (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) r += 1u;
+  return __uint_as_float(r);
 }
 
-__device__ __forceinline__ double load_b(const KChunk& c, int k, int n) {
+// FP32 -> FP64, exact, on the integer pipes (FP32 subnormals become zero).
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const int e = (int)((u >> 23) & 0xff);
+  const unsigned long long frac = u & 0x7FFFFFu;
+  if (e == 0) return __longlong_as_double((long long)sign);
+  if (e == 0xff) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull | (frac << 29)));
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(e - 127 + 1023) << 52) | (frac << 29)));
+}
+
+template <typename T>
+__device__ __forceinline__ T to_t(double v);
+template <>
+__device__ __forceinline__ double to_t<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float to_t<float>(double v) { return d2f_bits(v); }
+
+template <typename T>
+__device__ __forceinline__ double to_d(T v);
+template <>
+__device__ __forceinline__ double to_d<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ double to_d<float>(float v) { return f2d_bits(v); }
+
+// Row maps are sign-encoded: -1 = zero row, otherwise (row << 1) | negate.
+// Arithmetic in T (FP64, or FP32 with the operands converted first).
+template <typename T>
+__device__ __forceinline__ T load_a(const KChunk& c, int m, int k) {
+  long long row = m;
+  T scale = T(1);
+  if (c.amap) {
+    int r = c.amap[m];
+    if (r < 0) return T(0);
+    row = r >> 1;
+    if (r & 1) scale = T(-1);
+  }
+  if (c.aval) scale *= to_t<T>(c.aval[m]);
+  return scale * to_t<T>(c.A[row * c.a_m + (long long)k * c.a_k]);
+}
+
+template <typename T>
+__device__ __forceinline__ T load_b(const KChunk& c, int k, int n) {
   long long row = k;
-  double scale = 1.0;
+  T scale = T(1);
   if (c.bmap) {
     int r = c.bmap[k];
-    if (r < 0) return 0.0;
+    if (r < 0) return T(0);
     row = r >> 1;
-    if (r & 1) scale = -1.0;
+    if (r & 1) scale = T(-1);
   }
-  if (c.bval) scale *= c.bval[k];
-  return scale * c.B[row * c.b_k + (long long)n * c.b_n];
+  if (c.bval) scale *= to_t<T>(c.bval[k]);
+  return scale * to_t<T>(c.B[row * c.b_k + (long long)n * c.b_n]);
 }
 
 // One CTA computes a BM x BN tile of one output (16 x 16 threads, each a
@@ -75,20 +125,21 @@ __global__ void __launch_bounds__(THREADS) kc_gemm_kernel(const KTile* __restric
 #pragma unroll
         for (int j = 0; j < TN; ++j) {
           const int m = tile.m0 + ty * TM + i, n = tile.n0 + tx * TN + j;
-          if (m < out.M && n < out.N) acc[i][j] += (T)(c.alpha * load_a(c, m, n));
+          if (m < out.M && n < out.N) acc[i][j] += to_t<T>(c.alpha) * load_a<T>(c, m, n);
         }
       continue;
     }
+    const T alpha = to_t<T>(c.alpha);
     for (int k0 = 0; k0 < c.K; k0 += BK) {
       for (int e = tid; e < BM * BK; e += THREADS) {
         const int mm = e / BK, kk = e % BK;
         const int m = tile.m0 + mm, k = k0 + kk;
-        As[kk][mm] = (m < out.M && k < c.K) ? (T)(c.alpha * load_a(c, m, k)) : T(0);
+        As[kk][mm] = (m < out.M && k < c.K) ? alpha * load_a<T>(c, m, k) : T(0);
       }
       for (int e = tid; e < BN * BK; e += THREADS) {
         const int kk = e / BN, nn = e % BN;
         const int n = tile.n0 + nn, k = k0 + kk;
-        Bs[kk][nn] = (n < out.N && k < c.K) ? (T)load_b(c, k, n) : T(0);
+        Bs[kk][nn] = (n < out.N && k < c.K) ? load_b<T>(c, k, n) : T(0);
       }
       __syncthreads();
 #pragma unroll
@@ -112,11 +163,12 @@ __global__ void __launch_bounds__(THREADS) kc_gemm_kernel(const KTile* __restric
     for (int j = 0; j < TN; ++j) {
       const int m = tile.m0 + ty * TM + i, n = tile.n0 + tx * TN + j;
       if (m >= out.M || n >= out.N) continue;
+      const double v = to_d<T>(acc[i][j]);
       if (tile.part >= 0) {
-        scratch[out.part_off + (long long)tile.part * out.M * out.N + (long long)m * out.N + n] = (double)acc[i][j];
+        scratch[out.part_off + (long long)tile.part * out.M * out.N + (long long)m * out.N + n] = v;
       } else {
         double* p = out.C + (long long)m * out.c_m + (long long)n * out.c_n;
-        *p = out.accumulate ? (*p + (double)acc[i][j]) : (double)acc[i][j];
+        *p = out.accumulate ? (*p + v) : v;
       }
     }
 }

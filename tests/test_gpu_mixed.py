@@ -78,3 +78,23 @@ def test_mixed_sweep_matches_fp64(q, prec):
     e_ref, e_mix = np.array(e_ref), np.array(e_mix)
     assert np.max(np.abs(e_mix - e_ref) / np.abs(e_ref)) < 1e-6
     assert mixed_iters > 0
+
+
+def test_upper_node_fp32_products(q):
+    """Upper-node products of the low-precision phase (FP32 grouped GEMM whose
+    FP64 operands are converted to FP32 on the integer pipes) against FP64 at
+    every upper node: FP32 rounding only."""
+    L, chi = (4, 2, 2), 16
+    ref = q.TTN(q.Model(*L, **KW), chi, seed=4, precision="fp64")
+    mix = q.TTN(q.Model(*L, **KW), chi, seed=4, precision="tf32x3")
+    tree = ref.model.tree()
+    rng = np.random.default_rng(6)
+    upper = [i for i in range(len(tree)) if tree[i][2] == 1]
+    assert upper
+    for node in upper:
+        ref.move_center(node)
+        mix.move_center(node)
+        x = rng.standard_normal(ref.node_size(node))
+        y64 = ref.apply_heff(x)
+        ym = mix.apply_heff(x)
+        assert np.max(np.abs(ym - y64)) / np.max(np.abs(y64)) < 1e-5, node
