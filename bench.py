@@ -390,8 +390,10 @@ def run_native(args):
 
 
 def run_heff_only(args):
-    """Profiling aid: the workload state with its centre at bottom node 0
-    and --steps H_eff x products on device buffers (no sweep)."""
+    """Profiling aid: the workload state with its centre at --node, --warmup
+    untimed H_eff x products on device buffers (the tile-shape tuner settles),
+    --steps products timed with CUDA events, then one product between
+    cudaProfilerStart and cudaProfilerStop (for ncu --profile-from-start off)."""
     import torch
     import paper_2011_10658_gb300 as q
     torch.cuda.set_device(0)
@@ -400,12 +402,24 @@ def run_heff_only(args):
     s = q.TTN(q.Model(*L, Q=Q, **c), CHI, seed=SEED, precision=args.precision, stream=stream.cuda_stream)
     s.move_center(args.node)
     n = s.node_size(args.node)
-    x = torch.randn(n, dtype=torch.float64, device="cuda")
+    x = torch.randn(n, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
     y = torch.empty_like(x)
-    for _ in range(args.warmup + args.steps):
+    for _ in range(args.warmup):
         s.apply_heff_device(x.data_ptr(), y.data_ptr(), n)
     torch.cuda.synchronize()
-    print(json.dumps({"mode": "heff", "node": args.node, "size": n, "products": args.warmup + args.steps,
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        s.apply_heff_device(x.data_ptr(), y.data_ptr(), n)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / max(1, args.steps)
+    torch.cuda.profiler.start()
+    s.apply_heff_device(x.data_ptr(), y.data_ptr(), n)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print(json.dumps({"mode": "heff", "node": args.node, "size": n, "precision": args.precision,
+                      "ms_per_product": ms, "products_timed": args.steps,
                       "norm": float(y.norm().item())}), flush=True)
     s.close()
 
