@@ -217,6 +217,24 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- native arm
+def replica_seed(rank):
+    """Seed of the independent problem rank `rank` runs (replicas only)."""
+    return SEED + rank
+
+
+def reduce_over_ranks(elapsed_ms, flops, device):
+    """Whole-job timing of independent replicas: the slowest rank's time and
+    the flops of all ranks (one all-reduce each, no data-path collective)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([elapsed_ms, flops], device=device, dtype=torch.float64)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return mx[0].item(), sm[1].item()
+
+
 def run_native(args):
     import numpy as np
     import torch
@@ -233,7 +251,7 @@ def run_native(args):
     c = workloads.qed_couplings(G2)
     model = q.Model(*L, Q=Q, **c)
     # replicas only: rank r runs an independent problem from seed SEED + r
-    s = q.TTN(model, CHI, seed=SEED + rank, precision=args.precision, stream=stream.cuda_stream)
+    s = q.TTN(model, CHI, seed=replica_seed(rank), precision=args.precision, stream=stream.cuda_stream)
     s.set_profiling(True)
     energies = []
 
@@ -269,12 +287,7 @@ def run_native(args):
     kt = {k: s.kernel_timing(k) for k in ("tc_heff", "heff_simt_bottom", "heff_simt_upper", "move", "lanczos", "move_qr", "move_ops")}
     flops = sum(kt[k]["flops_alg"] for k in ("tc_heff", "heff_simt_bottom", "heff_simt_upper"))
     if world > 1:
-        t = torch.tensor([elapsed_ms, flops], device="cuda", dtype=torch.float64)
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = t.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        elapsed_ms, flops = mx[0].item(), sm[1].item()
+        elapsed_ms, flops = reduce_over_ranks(elapsed_ms, flops, "cuda")
     value = flops / (elapsed_ms * 1e-3) / 1e12
 
     # dominant kernel roofline (kernel classes only, not whole phases)
@@ -342,7 +355,7 @@ def run_native(args):
     # FP64 GPU path on the same workload and sweeps for |dE|/|E|
     compare = None
     if args.compare_fp64 and args.precision != "fp64" and rank == 0:
-        r = q.TTN(model, CHI, seed=SEED + rank, precision="fp64", stream=stream.cuda_stream)
+        r = q.TTN(model, CHI, seed=replica_seed(rank), precision="fp64", stream=stream.cuda_stream)
         e64, t64 = [], []
         for _ in range(args.warmup + args.steps):
             torch.cuda.synchronize()
