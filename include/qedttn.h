@@ -148,13 +148,15 @@ typedef struct {
 int ttn_sweep(ttn_state *s, int32_t n_sweeps, double tol, int32_t max_krylov, ttn_sweep_stats *out);
 /* Mixed precision (QED_PREC_TF32 / QED_PREC_BF16): bottom-node updates run
  * Lanczos with tensor-core H_eff products until the residual reaches
- * max(tol, mixed_tol) (or stops improving), then continue from that Ritz
+ * max(0.3 tol, mixed_tol) (or stops improving), then continue from that Ritz
  * vector with FP64 products until the FP64 residual reaches tol.  Default
  * mixed_tol: 1e-7 (TF32X3), 1e-5 (TF32), 1e-4 (BF16). */
 int ttn_set_mixed_tol(ttn_state *s, double mixed_tol);
 /* n_sweeps sweeps of n independent problems together (batching of
  * independent ground-state problems, e.g. several charge sectors and
- * couplings).  The states must share the lattice size, the precision and
+ * couplings; the paper's finite-density results scan the charge Q, Results,
+ * each value a separate ground-state search -- running several at once has
+ * no counterpart there).  The states must share the lattice size, the precision and
  * the CUDA stream; sector tables, couplings and seeds may differ.  The
  * problems update each node together: per-problem centre moves, then a
  * lockstep Lanczos (same algorithm as ttn_sweep) whose H_eff products for
@@ -239,7 +241,7 @@ int ttn_apply_heff(ttn_state *s, const double *x, double *y, int64_t n);
 /* Same with device buffers on the state's stream (no host copies). */
 int ttn_apply_heff_device(ttn_state *s, const double *x_device, double *y_device, int64_t n);
 
-/* Checkpoint.  ttn_save moves the centre to the root (so the file holds a
+/* Checkpoint (no counterpart in the paper).  ttn_save moves the centre to the root (so the file holds a
  * tree isometric towards the root) and writes: the 8-byte tag "QEDTTN01",
  * the model parameters (Lx, Ly, Lz, boundary, Q as int32; t, m, ge2, cB, nu as
  * FP64), chi, precision (int32), seed (uint64), the node count (int32), the
@@ -252,7 +254,10 @@ int ttn_apply_heff_device(ttn_state *s, const double *x_device, double *y_device
 int ttn_save(ttn_state *s, const char *path);
 int ttn_load(const qed_model *m, const char *path, void *cuda_stream, ttn_state **out);
 
-/* Differentiation of E(psi; couplings) = psi^T H_eff psi / psi^T psi.
+/* Differentiation of E(psi; couplings) = psi^T H_eff psi / psi^T psi.  The
+ * paper updates tensors by the eigensolver only (Methods, steps (i)-(iii));
+ * the gradient and the gradient step are additions, and dE/dcoupling rests
+ * on Eq. (1) + Eq. (16) being linear in each coupling.
  *
  * y = H_eff^T x at the current centre with every product term transposed
  * (A^T (x) B^T (x) C^T on the three legs, monomial site operators through
