@@ -158,3 +158,19 @@ def test_every_tile_shape_matches_oracle(q, shape, monkeypatch):
         e_ref = ref.optimize_node(idx, tol=1e-12)
         e = s.optimize_node(idx, tol=1e-12, max_krylov=64)
         assert abs(e - e_ref) < REL_FP64 * abs(e_ref)
+
+
+def test_plain_workload_matches_stored_oracle_sweep(q):
+    """The plain-method workload (2x2x2, chi = 8, seed 0, tol 1e-12) swept by
+    the library reproduces the oracle's stored node energies
+    (tests/golden/plain_2x2x2_chi8.txt, written by make_plain_2x2x2.py)."""
+    import os
+    import workloads
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "plain_2x2x2_chi8.txt")
+    rows = [line.split() for line in open(path) if not line.startswith("#")]
+    c = workloads.qed_couplings(1.0)
+    s = q.TTN(q.Model(2, 2, 2, Q=0, **c), 8, seed=0)
+    assert [int(r[1]) for r in rows] == s.model.sweep_order().tolist()
+    for _, node, e in rows:
+        got = s.optimize_node(int(node), tol=1e-12, max_krylov=64)
+        assert abs(got - float(e)) < REL_FP64 * abs(float(e)), (node, got, e)

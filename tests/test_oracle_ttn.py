@@ -83,3 +83,18 @@ def test_energy_split_by_class(swept_2x2x1):
     pen = ttn.expectation(s, model.class_only(p, "nu"))
     assert abs(total - energies[-1]) < 1e-9
     assert abs(parts + pen - total) < 1e-10
+
+
+def test_plain_workload_stored_sweep_reproduces():
+    """The stored plain-workload sweep (tests/golden/plain_2x2x2_chi8.txt) is
+    what the oracle computes; the GPU test reads the stored file."""
+    import os
+    import workloads
+    from oracle import model as _model, ttn as _ttn
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "plain_2x2x2_chi8.txt")
+    rows = [line.split() for line in open(path) if not line.startswith("#")]
+    s = _ttn.TTN(_model.Params(2, 2, 2, Q=0, **workloads.qed_couplings(1.0)), 8, 0)
+    energies = s.sweep(tol=1e-12)
+    assert len(energies) == len(rows)
+    for (_, _, e), got in zip(rows, energies):
+        assert abs(got - float(e)) < 1e-10 * abs(float(e))
