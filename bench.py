@@ -301,10 +301,30 @@ def run_native(args):
         peak = pk["bf16_tflops_sustained"] * (1.1 / 2.25)
         bound, peak_note = "tensor", f"TF32 dense = {src} sustained BF16 {pk['bf16_tflops_sustained']} x 1.1/2.25"
         traffic = traffic_from_profile(os.path.join(ROOT, "paper_2011_10658_gb300", "csrc", "kernels_tc.cu"))
+    elif dom == "heff_simt_bottom" or args.precision == "fp64":
+        # FP64 products: GB300's FP64 rate (nominal 1.25 TFLOP/s)
+        peak, bound, peak_note, traffic = 1.25, "alu", "FP64 SIMT, nominal 1.25 TFLOP/s", None
     else:
         # FP32 SIMT: 152 SMs x 128 lanes x 2 flops x max SM clock
         peak = 152 * 128 * 2 * (pk.get("sm_max_mhz", 2070.0) * 1e6) / 1e12
         bound, peak_note, traffic = "alu", "FP32 SIMT 152 x 128 x 2 x 2070 MHz", None
+    # every product class and the FP64 operator updates against their own peaks
+    # (context for the dominant-class roofline above; FP64 SIMT peak from the
+    # nominal 1.25 TFLOP/s of this part, FP32 SIMT 152 x 128 x 2 x max clock)
+    fp64_peak = 1.25
+    fp32_peak = 152 * 128 * 2 * (pk.get("sm_max_mhz", 2070.0) * 1e6) / 1e12
+    tf32_peak = pk["bf16_tflops_sustained"] * (1.1 / 2.25)
+    class_rates = {}
+    for k, pkv, unit_note in (("tc_heff", tf32_peak, "TF32 tensor (measured BF16 sustained x 1.1/2.25)"),
+                              ("heff_simt_bottom", fp64_peak, "FP64 SIMT (nominal)"),
+                              ("heff_simt_upper", fp64_peak if args.precision == "fp64" else fp32_peak,
+                               "FP64 SIMT (nominal)" if args.precision == "fp64" else "FP32 SIMT (mostly)"),
+                              ("move_ops", fp64_peak, "FP64 SIMT (nominal)")):
+        v = kt[k]
+        if v["ms"] > 0 and v["flops_alg"] > 0:
+            r = v["flops_alg"] / (v["ms"] * 1e-3) / 1e12
+            class_rates[k] = {"tflops": r, "peak": pkv, "frac": r / pkv, "peak_source": unit_note,
+                              "ms": v["ms"], "launches": v["launches"]}
     roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_source": peak_note,
                 "launches": d["launches"], "ms_per_launch": per_launch_ms,
@@ -392,7 +412,7 @@ def run_native(args):
             "sweep_s": elapsed_ms / args.steps / 1e3,
             "energy": energies[-1],
             "matvecs_per_sweep": total_mv / args.steps, "mixed_matvecs_per_sweep": mixed_mv / args.steps,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "roofline": roofline, "class_rates": class_rates, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches, "kernels": kt, "per_update_vs_fp64": per_update,
             "fp64_trajectory_comparison": compare,
         }

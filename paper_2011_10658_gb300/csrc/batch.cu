@@ -63,7 +63,7 @@ void upload_vec(T*& dptr, size_t& cap, const std::vector<T>& host, cudaStream_t 
   if (host.size() > cap) {
     if (dptr) cudaFree(dptr);
     cap = host.size();
-    cudaMalloc(&dptr, cap * sizeof(T));
+    device_alloc((void**)&dptr, cap * sizeof(T), "grouped plan arrays");
   }
   cudaMemcpyAsync(dptr, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice, s);
 }

@@ -43,6 +43,8 @@ void qed_set_last_error(const char* msg) { g_err = msg; }
     __VA_ARGS__                                         \
   } catch (const std::bad_alloc&) {                     \
     return fail(QED_ENOMEM, "out of host memory");      \
+  } catch (const qed::DeviceAllocError& ex) {           \
+    return fail(QED_ENOMEM, ex.what());                 \
   } catch (const std::exception& ex) {                  \
     return fail(QED_EINVAL, ex.what());                 \
   } catch (...) {                                       \

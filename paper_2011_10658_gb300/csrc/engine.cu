@@ -70,6 +70,16 @@ void Layout::build(const Sectors& a, const Sectors& b, const Sectors& c, int shi
   size = off;
 }
 
+void device_alloc(void** p, size_t bytes, const char* what) {
+  *p = nullptr;
+  const cudaError_t e = cudaMalloc(p, bytes == 0 ? 16 : bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    throw DeviceAllocError(std::string(what) + ": " + cudaGetErrorString(e));
+  }
+}
+
 // ------------------------------------------------------------------ KPlan
 int KPlan::add_output(double* C, long long c_m, long long c_n, int M, int N, int accumulate) {
   auto key = std::make_tuple((uintptr_t)C, c_m, c_n, M, N);
@@ -223,7 +233,7 @@ static void grow_upload(T*& dptr, size_t& cap, const std::vector<T>& host, cudaS
   if (host.size() > cap) {
     if (dptr) cudaFree(dptr);
     cap = host.size() + host.size() / 2 + 16;
-    cudaMalloc(&dptr, cap * sizeof(T));
+    device_alloc((void**)&dptr, cap * sizeof(T), "plan arrays");
   }
   cudaMemcpyAsync(dptr, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice, s);
 }
@@ -276,8 +286,7 @@ static KChunk make_chunk() {
 void* Engine::dalloc(size_t bytes) {
   void* p = nullptr;
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(&p, bytes);
-  if (e != cudaSuccess) throw std::runtime_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  device_alloc(&p, bytes, "device tensors");
   allocs_.push_back(p);
   bytes_ += (long long)bytes;
   track(p, bytes);
@@ -339,7 +348,7 @@ void Engine::ensure_scratch(long long elems) {
   if (elems <= scratch_elems_) return;
   if (scratch_) { untrack(scratch_); cudaFree(scratch_); }
   scratch_elems_ = elems + elems / 2;
-  cudaMalloc(&scratch_, scratch_elems_ * sizeof(double));
+  device_alloc((void**)&scratch_, scratch_elems_ * sizeof(double), "split-K scratch");
   track(scratch_, scratch_elems_ * sizeof(double));
 }
 
@@ -348,7 +357,7 @@ void Engine::ensure_zpool(long long elems) {
   clear_plan_caches();   // cached plans point into the old pool
   if (zpool_) { untrack(zpool_); cudaFree(zpool_); }
   zpool_elems_ = elems + elems / 4;
-  cudaMalloc(&zpool_, zpool_elems_ * sizeof(double));
+  device_alloc((void**)&zpool_, zpool_elems_ * sizeof(double), "Z pool");
   track(zpool_, zpool_elems_ * sizeof(double));
 }
 
@@ -942,10 +951,10 @@ int Engine::qr_toward(int node, int leg, double* Rout) {
       d.max_n = std::max(d.max_n, S.dim[i]);
     }
     d.count = (int)nn.size();
-    cudaMalloc(&d.off, off.size() * sizeof(long long));
-    cudaMalloc(&d.n, nn.size() * sizeof(int));
-    cudaMalloc(&d.ld, ld.size() * sizeof(int));
-    cudaMalloc(&d.status, nn.size() * sizeof(int));
+    device_alloc((void**)&d.off, off.size() * sizeof(long long), "QR descriptors");
+    device_alloc((void**)&d.n, nn.size() * sizeof(int), "QR descriptors");
+    device_alloc((void**)&d.ld, ld.size() * sizeof(int), "QR descriptors");
+    device_alloc((void**)&d.status, nn.size() * sizeof(int), "QR descriptors");
     cudaMemcpyAsync(d.off, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice, stream_);
     cudaMemcpyAsync(d.n, nn.data(), nn.size() * sizeof(int), cudaMemcpyHostToDevice, stream_);
     cudaMemcpyAsync(d.ld, ld.data(), ld.size() * sizeof(int), cudaMemcpyHostToDevice, stream_);
@@ -1115,10 +1124,10 @@ int Engine::qr_gram_schmidt(int node, int leg, double* Rout) {
       long long* d_w = nullptr;
       long long* d_r = nullptr;
       int *d_rows = nullptr, *d_cols = nullptr;
-      cudaMalloc(&d_w, ns * sizeof(long long));
-      cudaMalloc(&d_r, ns * sizeof(long long));
-      cudaMalloc(&d_rows, ns * sizeof(int));
-      cudaMalloc(&d_cols, ns * sizeof(int));
+      device_alloc((void**)&d_w, ns * sizeof(long long), "QR descriptors");
+      device_alloc((void**)&d_r, ns * sizeof(long long), "QR descriptors");
+      device_alloc((void**)&d_rows, ns * sizeof(int), "QR descriptors");
+      device_alloc((void**)&d_cols, ns * sizeof(int), "QR descriptors");
       cudaMemcpyAsync(d_w, woff.data(), ns * sizeof(long long), cudaMemcpyHostToDevice, stream_);
       cudaMemcpyAsync(d_r, roff.data(), ns * sizeof(long long), cudaMemcpyHostToDevice, stream_);
       cudaMemcpyAsync(d_rows, ri.data(), ns * sizeof(int), cudaMemcpyHostToDevice, stream_);
@@ -2377,7 +2386,7 @@ int Engine::site_probabilities(std::vector<double>* probs) {
   std::vector<double*> rho(n, nullptr);
   probs->assign((size_t)lat_.n_sites() * kLocalDim, 0.0);
   double* one = nullptr;
-  cudaMalloc(&one, sizeof(double));
+  device_alloc((void**)&one, sizeof(double), "density matrix");
   track(one, sizeof(double));
   const double v1 = 1.0;
   cudaMemcpyAsync(one, &v1, sizeof(double), cudaMemcpyHostToDevice, stream_);
@@ -2394,7 +2403,7 @@ int Engine::site_probabilities(std::vector<double>* probs) {
     for (int leg = 0; leg < 2 && rc == 0; ++leg) {
       const int d = L.leg[leg].total();
       double* red = nullptr;
-      cudaMalloc(&red, (size_t)d * d * sizeof(double));
+      device_alloc((void**)&red, (size_t)d * d * sizeof(double), "density matrix");
       track(red, (size_t)d * d * sizeof(double));
       tofree.push_back(red);
       cudaMemsetAsync(red, 0, (size_t)d * d * sizeof(double), stream_);

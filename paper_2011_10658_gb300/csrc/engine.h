@@ -6,6 +6,7 @@
 #include <functional>
 #include <map>
 #include <memory>
+#include <stdexcept>
 #include <string>
 #include <tuple>
 #include <unordered_map>
@@ -17,6 +18,13 @@
 namespace qed {
 
 constexpr int kMaxKrylov = 128;   // largest Lanczos basis
+
+// A device allocation that failed (reported as QED_ENOMEM at the C ABI).
+struct DeviceAllocError : std::runtime_error {
+  explicit DeviceAllocError(const std::string& what) : std::runtime_error(what) {}
+};
+// cudaMalloc that throws DeviceAllocError instead of returning an error code.
+void device_alloc(void** p, size_t bytes, const char* what);
 
 enum Precision { PREC_FP64 = 0, PREC_TF32 = 1, PREC_BF16 = 2, PREC_TF32X3 = 3 };
 
