@@ -6,7 +6,7 @@ genuinely local (fermion-even) site operators, so sites can be treated as
 plain tensor factors (Methods: the factorisations of Eq. (15) and of the
 plaquette make every operator local and bosonic).
 
-Readings of the paper used here (listed in the design doc as well):
+Readings of the paper used here (the library takes the same ones):
 * couplings t, m, ge2 = g_e^2, cB, nu are independent inputs; the plaquette
   enters as -cB * sum(box + h.c.) (Eq. (1) third line with cB = g_m^2/2);
 * open boundaries keep all six half-links at every site; half-links that

@@ -2094,11 +2094,12 @@ int Engine::kernel_timing(KernelTiming out[KC_COUNT]) {
 }
 
 // ------------------------------------------------------------------ Lanczos
-// Symmetric Lanczos with full (twice-applied classical Gram-Schmidt)
-// reorthogonalisation, started from the current tensor; the lowest Ritz
-// pair of the tridiagonal is found on the device.  Stops when the
-// residual estimate |beta_k s_k| <= tol |theta|, restarting from the Ritz
-// vector when the Krylov space is full.
+// Symmetric Lanczos with full reorthogonalisation (classical Gram-Schmidt,
+// a second pass when the first removed more than half of the norm), started
+// from the current tensor; the lowest Ritz pair of the tridiagonal is found
+// on the device.  Stops when the residual estimate |beta_k s_k| <= tol
+// |theta|; when the Krylov space is full, a thick restart keeps the lowest
+// Ritz vectors.
 int Engine::lanczos(int node, double tol, int max_krylov, bool mixed, int max_restarts, double* energy, double* resid,
                     int* iters) {
   cudaEvent_t e0 = nullptr;
