@@ -272,3 +272,27 @@ def test_sweep_order_properties(L):
         return sum(dist(x, y) for x, y in zip([len(nodes) - 1] + list(seq[:-1]), seq))
 
     assert moves(order) < moves(list(range(len(nodes))))
+
+
+def _strong(g2, Q=0):
+    c = dict(t=1.0, m=1.0, ge2=g2, cB=1.0 / (2.0 * g2), nu=10.0 * max(1.0, g2 / 2.0))
+    return model.Params(2, 2, 1, Q=Q, **c)
+
+
+def test_strong_coupling_second_order():
+    """g^2 -> infinity (Q = 0): the ground state is the bare staggered vacuum,
+    E0 = -m N / 2, and second-order perturbation theory in t adds, per link,
+    -t^2 / (2 m + g^2 / 2) (one hop creates a particle-antiparticle pair, cost
+    2m, joined by one unit of electric flux, cost g^2/2).  The exact energy's
+    second-order part tends to that value with a relative error that falls
+    at least 4x for every 4x in g^2."""
+    n_sites, n_links, m, t = 4, 4, 1.0, 1.0
+    e0 = -m * n_sites / 2.0
+    errs = []
+    for g2 in (10.0, 40.0, 160.0):
+        e = ed.config_ed(_strong(g2))
+        ept = e0 - n_links * t * t / (2.0 * m + g2 / 2.0)
+        errs.append(abs((e - e0) / (ept - e0) - 1.0))
+        assert e < e0
+    assert errs[2] < 1e-3
+    assert errs[1] < errs[0] / 4 and errs[2] < errs[1] / 4

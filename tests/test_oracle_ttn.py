@@ -98,3 +98,24 @@ def test_plain_workload_stored_sweep_reproduces():
     assert len(energies) == len(rows)
     for (_, _, e), got in zip(rows, energies):
         assert abs(got - float(e)) < 1e-10 * abs(float(e))
+
+
+def test_strong_coupling_chi1_pair_product():
+    """chi = 1 on 2x2x1 makes the TTN a product of the two bottom-node pairs
+    (x-neighbours).  As g^2 grows it tends to the confined vacuum dressed by
+    the pair fluctuations of the two links inside the pairs: E0 - 2 t^2 /
+    (2 m + g^2 / 2) to second order, between the exact energy and E0."""
+    from oracle import ed
+    errs = []
+    for g2, tol in ((40.0, 5e-3), (160.0, 5e-4)):
+        c = dict(t=1.0, m=1.0, ge2=g2, cB=1.0 / (2.0 * g2), nu=10.0 * max(1.0, g2 / 2.0))
+        p = model.Params(2, 2, 1, Q=0, **c)
+        s = ttn.TTN(p, 1, 0)
+        s.sweep(tol=1e-12)
+        e = s.sweep(tol=1e-12)[-1]
+        e0 = -2.0
+        ept = e0 - 2.0 / (2.0 + g2 / 2.0)
+        assert ed.config_ed(p) - 1e-9 <= e <= e0
+        errs.append(abs((e - e0) / (ept - e0) - 1.0))
+        assert errs[-1] < tol
+    assert errs[1] < errs[0] / 4
