@@ -1,0 +1,84 @@
+"""Parity at the benchmark's full size (4x4x4 open lattice, chi = 64, seed 1,
+Q = 0, the state bench.py times): the seeded isometric start equals the
+oracle's at every node, and properties that hold at any size are checked
+where the oracle's full operator contractions would take too long on the
+host -- the adjoint equals the transpose and the forward product, the energy
+does not depend on the centre position, the total charge is Q, and a
+split-TF32 node update equals the FP64 one on the identical H_eff."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import model as omodel, ttn as ottn
+
+from ttn_layout import to_layout
+
+pytestmark = pytest.mark.gpu
+
+L, CHI, SEED, Q = (4, 4, 4), 64, 1, 0
+
+
+@pytest.fixture(scope="module")
+def q():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2011_10658_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def _model(q):
+    return q.Model(*L, Q=Q, **workloads.qed_couplings(1.0))
+
+
+def test_initial_tensors_full_size(q):
+    ref = ottn.TTN(omodel.Params(*L, Q=Q, **workloads.qed_couplings(1.0)), CHI, SEED, build_ops=False)
+    s = q.TTN(_model(q), CHI, seed=SEED)
+    for idx in range(len(ref.nodes)):
+        got = s.node_export(idx)
+        want = to_layout(ref.T[idx], ref.labels[idx])
+        assert got.shape == want.shape, idx
+        assert np.max(np.abs(got - want)) < 1e-12, idx
+
+
+def test_properties_full_size(q):
+    import torch
+    s = q.TTN(_model(q), CHI, seed=SEED)
+    e_root = s.energy()[0]
+    rng = np.random.default_rng(8)
+    for node in (0, 40, 61):
+        s.move_center(node)
+        n = s.node_size(node)
+        u = torch.tensor(rng.standard_normal(n), dtype=torch.float64, device="cuda")
+        v = torch.tensor(rng.standard_normal(n), dtype=torch.float64, device="cuda")
+        hv, htu, htv = (torch.empty_like(u) for _ in range(3))
+        s.apply_heff_device(v.data_ptr(), hv.data_ptr(), n)
+        s.apply_heff_adjoint_device(u.data_ptr(), htu.data_ptr(), n)
+        s.apply_heff_adjoint_device(v.data_ptr(), htv.data_ptr(), n)
+        torch.cuda.synchronize()
+        lhs, rhs = float(u @ hv), float(htu @ v)
+        assert abs(lhs - rhs) <= 1e-11 * max(1.0, abs(lhs)), node
+        assert float((htv - hv).abs().max()) <= 1e-11 * float(hv.abs().max()), node
+        # the state's energy seen from this centre
+        e_here, _ = s.energy_grad_device(node)
+        assert abs(e_here - e_root) < 1e-10 * abs(e_root), node
+    qx = s.measure("qx")
+    assert abs(float(np.sum(qx)) - Q) < 1e-9
+
+
+def test_mixed_update_equals_fp64_full_size(q):
+    """Node updates from identical states and identical H_eff, split-TF32 with
+    the FP64 correction against FP64 throughout, at the tolerance the
+    benchmark uses."""
+    tol = 1e-6
+    s = q.TTN(_model(q), CHI, seed=SEED, precision="tf32x3")
+    for node in (0, 48):
+        s.move_center(node)
+        t0 = s.node_export(node)
+        s.set_precision("fp64")
+        e64 = s.optimize_node(node, tol=tol, max_krylov=64)
+        s.node_import(node, t0)
+        s.set_precision("tf32x3")
+        em = s.optimize_node(node, tol=tol, max_krylov=64)
+        assert abs(em - e64) < 1e-6 * abs(e64), (node, em, e64)
