@@ -137,7 +137,9 @@ def test_tree_equal(q, L):
 
 
 @pytest.mark.parametrize("L,chi,Q", [((2, 2, 2), 8, 0), ((2, 2, 1), 12, 0), ((4, 4, 4), 64, 0),
-                                     ((4, 4, 4), 48, 16), ((4, 4, 4), 32, 4), ((4, 4, 4), 48, 6)])
+                                     ((4, 4, 4), 48, 16), ((4, 4, 4), 32, 4), ((4, 4, 4), 48, 6),
+                                     ((4, 4, 4), 48, 2), ((4, 4, 4), 48, 10), ((4, 4, 4), 48, 14),
+                                     ((4, 4, 4), 1, 0), ((2, 2, 1), 4, 2)])
 def test_sector_table_equal(q, L, chi, Q):
     assert q.Model(*L, Q=Q).sectors(chi) == otree.sector_table(omodel.Params(*L, Q=Q), chi)
 
