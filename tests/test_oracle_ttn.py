@@ -119,3 +119,31 @@ def test_strong_coupling_chi1_pair_product():
         errs.append(abs((e - e0) / (ept - e0) - 1.0))
         assert errs[-1] < tol
     assert errs[1] < errs[0] / 4
+
+
+def test_site_observables_against_dressed_ed():
+    """Two sites: the TTN (one node holding both sites, exact) gives the same
+    single-site occupations <psi^dag psi>_x as the ground vector of the full
+    dressed-space Hamiltonian, and each site's probabilities sum to one."""
+    import scipy.sparse.linalg as spla
+    from oracle import basis
+    p = model.Params(2, 1, 1, t=0.8, m=0.6, ge2=1.2, cB=0.5, nu=12.0, Q=0)
+    H, qv, _ = ed.dressed_hamiltonian(p)
+    sel = np.nonzero(qv == p.Q)[0]
+    vals, vecs = spla.eigsh(H[sel][:, sel], k=1, which="SA", tol=1e-14)
+    v = np.zeros(H.shape[0])
+    v[sel] = vecs[:, 0]
+    w = (v * v).reshape(basis.D_LOCAL, basis.D_LOCAL)
+    lat = model.Lattice(2, 1, 1)
+    phi_ed = [float(w.sum(axis=1) @ basis.enumerate_basis(lat.parity(0))[:, 0]),
+              float(w.sum(axis=0) @ basis.enumerate_basis(lat.parity(1))[:, 0])]
+    s = ttn.TTN(p, 8, 0)
+    e = s.sweep(tol=1e-12)[-1]
+    assert abs(e - vals[0]) < 1e-10 * abs(vals[0])
+    obs = s.observables()
+    for x in range(2):
+        assert abs(obs["phi"][x] - phi_ed[x]) < 1e-8, (x, obs["phi"][x], phi_ed[x])
+    probs = s.site_probabilities()
+    for x in range(2):
+        assert abs(np.sum(probs[x]) - 1.0) < 1e-12
+        assert np.min(probs[x]) > -1e-14
