@@ -143,6 +143,10 @@ def test_site_observables_against_dressed_ed():
     obs = s.observables()
     for x in range(2):
         assert abs(obs["phi"][x] - phi_ed[x]) < 1e-8, (x, obs["phi"][x], phi_ed[x])
+    # the link field of Eq. (10) at the lower site: E = 1 - k_{x,+x}
+    k_plus_x = basis.enumerate_basis(lat.parity(0))[:, basis.COL_K][:, model.plus(0)].astype(float)
+    e_link_ed = 1.0 - float(w.sum(axis=1) @ k_plus_x)
+    assert abs(obs["E_link"][0] - e_link_ed) < 1e-8
     probs = s.site_probabilities()
     for x in range(2):
         assert abs(np.sum(probs[x]) - 1.0) < 1e-12
