@@ -420,15 +420,22 @@ class TTN:
         out["delta_L"] = dL
         out["rho"] = float(np.mean(out["n"]))
         out["Q"] = float(np.sum(out["q"]))
-        # sigma(l): sites at lattice distance l (>= 1) from the closest boundary
-        dims = lat.dims()
+        # sigma(l): mean <psi^dag psi> over the sites of surface layer l
         layers = {}
         for s in range(lat.n_sites):
-            c = lat.coords(s)
-            l = 1 + min(min(c[a], dims[a] - 1 - c[a]) for a in range(3))
-            layers.setdefault(l, []).append(out["phi"][s])
+            layers.setdefault(surface_layer(lat, s), []).append(out["phi"][s])
         out["sigma"] = [float(np.mean(layers[l])) for l in sorted(layers)]
         return out
+
+
+def surface_layer(lat, s):
+    """Layer index l of site s for the surface charge density sigma(l) of
+    Eq. (16a): l = 1 on the outer surface of the open lattice, l = 2 one
+    site further in, and so on (one plus the number of sites between s and
+    the closest boundary face)."""
+    c = lat.coords(s)
+    dims = lat.dims()
+    return 1 + min(min(c[a], dims[a] - 1 - c[a]) for a in range(3))
 
 
 def expectation(state: TTN, p: _model.Params):
