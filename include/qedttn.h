@@ -152,6 +152,15 @@ int ttn_sweep(ttn_state *s, int32_t n_sweeps, double tol, int32_t max_krylov, tt
  * vector with FP64 products until the FP64 residual reaches tol.  Default
  * mixed_tol: 1e-7 (TF32X3), 1e-5 (TF32), 1e-4 (BF16). */
 int ttn_set_mixed_tol(ttn_state *s, double mixed_tol);
+/* Bound of every mbarrier wait inside the tensor-core kernels of this state,
+ * in polls (each poll is one mbarrier test plus a 32 ns sleep); polls < 0
+ * restores the default (2^22 polls, about a quarter of a second).  A wait
+ * that runs out sets a device flag, the kernel drains the MMAs it issued,
+ * frees its tensor memory and returns; the node update then returns
+ * QED_ETIMEOUT and the state stays usable.  No counterpart in the paper: a
+ * failure-detection control (polls = 0 makes every such wait give up at
+ * once, which is how the tests reach that path without a GPU fault). */
+int ttn_set_wait_limit(ttn_state *s, int64_t polls);
 /* n_sweeps sweeps of n independent problems together (batching of
  * independent ground-state problems, e.g. several charge sectors and
  * couplings; the paper's finite-density results scan the charge Q, Results,
@@ -171,8 +180,12 @@ int ttn_batch_sweep(ttn_state *const *states, int32_t n, int32_t n_sweeps, doubl
 /* Switch the product precision of an existing state (QED_PREC_*); resets
  * mixed_tol to its default for that precision. */
 int ttn_set_precision(ttn_state *s, int precision);
-/* Last node update: FP64 and mixed Lanczos iterations, |beta s| / |theta|. */
-int ttn_last_update(ttn_state *s, int32_t *iters_fp64, int32_t *iters_mixed, double *rel_residual);
+/* Last node update: FP64 and mixed Lanczos iterations, |beta s| / |theta|
+ * of the final (FP64) Ritz pair, and for a mixed update the Ritz value and
+ * relative residual that the low-precision phase reached before the FP64
+ * correction (NaN after an FP64 update).  Any output may be NULL. */
+int ttn_last_update(ttn_state *s, int32_t *iters_fp64, int32_t *iters_mixed, double *rel_residual,
+                    double *ritz_mixed, double *rel_residual_mixed);
 
 /* Kernel timing with CUDA events on the state's stream (off by default).
  * kernel_class: 0 = tensor-core bottom-node H_eff, 1 = SIMT bottom-node
@@ -228,7 +241,9 @@ int ttn_node_import(ttn_state *s, int32_t node, const double *buf, int64_t n);
  * for every node i; the tree must be isometric towards the root (as after
  * ttn_sweep, or ttn_node_export of such a state).  Copies them to the device
  * (pinned host memory makes the copies asynchronous), rebuilds every
- * renormalized operator and puts the centre at the root. */
+ * renormalized operator and puts the centre at the root.  QED_ENAN if an
+ * entry is NaN or infinite (looked for on the device after the copies; the
+ * state's tensors are then undefined until a load succeeds). */
 int ttn_load_tensors(ttn_state *s, const double *const *bufs, const int64_t *sizes, int32_t n_nodes);
 /* Kernels launched by the library in this process so far (all states). */
 int qed_launch_count(int64_t *count);
@@ -294,12 +309,26 @@ int ttn_gradient_step(ttn_state *s, double eta, double *e_before, double *e_afte
  * 4 MiB that every GPU loading the library holds until the process exits.
  * The first call on a device looks up that array's device address once
  * (cudaGetSymbolAddress); make that first call before any stream capture.
- * Every call rewrites the array, so calls that overlap on the GPU (from
- * different streams or threads) race; calls on one stream are ordered.
- * The centre must be a bottom node whose row maps and environment
- * operators exist (any state whose centre was moved there by ttn_move_center
- * or a sweep).  Errors: QED_EUNSUPPORTED for another centre or a work list
- * larger than the array, QED_EINVAL for a size mismatch. */
+ * The work list is written on the host into a static pageable buffer and
+ * copied to the array with cudaMemcpyAsync on the state's stream; a copy
+ * from pageable memory first waits for the work already queued on that
+ * stream and returns once the host buffer has been read, so each call
+ * blocks the calling thread until the stream's earlier work is done (the
+ * kernel launch itself is asynchronous).
+ * Every call rewrites the array, so kernels of calls that overlap on the GPU
+ * race.  Two states have two different streams: calls on different
+ * ttn_state objects (from one thread or several) can overlap, and the caller
+ * must synchronise between them (for example cudaStreamSynchronize on the
+ * first state's stream before calling on the second).  Calls on one state
+ * are ordered on its stream.
+ * The centre must be a bottom node whose row maps and environment operators
+ * exist: any bottom node that ttn_move_center or a sweep moved the centre to
+ * has them, because every operator update that leaves it builds them.  A
+ * bottom node that is also the root (a two-site lattice) is never left by an
+ * operator update; there one call of ttn_apply_heff_device at that centre
+ * builds the row maps first.  Errors: QED_EUNSUPPORTED for another centre,
+ * a missing row map (the message names it) or a work list larger than the
+ * array, QED_EINVAL for a size mismatch. */
 int ttn_apply_heff_device_noalloc(ttn_state *s, const double *x_device, double *y_device, int64_t n);
 
 const char *qed_last_error(void);

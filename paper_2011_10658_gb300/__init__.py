@@ -160,10 +160,16 @@ class TTN:
     def set_mixed_tol(self, tol):
         check(lib().ttn_set_mixed_tol(self._h, tol))
 
+    def set_wait_limit(self, polls):
+        check(lib().ttn_set_wait_limit(self._h, int(polls)))
+
     def last_update(self):
         a, b, r = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
-        check(lib().ttn_last_update(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(r)))
-        return dict(iters_fp64=a.value, iters_mixed=b.value, rel_residual=r.value)
+        th, rm = ctypes.c_double(), ctypes.c_double()
+        check(lib().ttn_last_update(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(r), ctypes.byref(th),
+                                    ctypes.byref(rm)))
+        return dict(iters_fp64=a.value, iters_mixed=b.value, rel_residual=r.value, ritz_mixed=th.value,
+                    rel_residual_mixed=rm.value)
 
     def set_profiling(self, on=True):
         check(lib().ttn_set_profiling(self._h, 1 if on else 0))

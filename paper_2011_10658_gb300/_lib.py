@@ -52,8 +52,9 @@ SIGNATURES = [
                                  ctypes.POINTER(SweepStats)]),
     ("ttn_optimize_node", c_int, [c_void_p, c_int32, c_double, c_int32, c_double_p]),
     ("ttn_set_mixed_tol", c_int, [c_void_p, c_double]),
+    ("ttn_set_wait_limit", c_int, [c_void_p, c_int64]),
     ("ttn_set_precision", c_int, [c_void_p, c_int]),
-    ("ttn_last_update", c_int, [c_void_p, c_int32_p, c_int32_p, c_double_p]),
+    ("ttn_last_update", c_int, [c_void_p, c_int32_p, c_int32_p, c_double_p, c_double_p, c_double_p]),
     ("ttn_set_profiling", c_int, [c_void_p, c_int]),
     ("ttn_reset_timing", c_int, [c_void_p]),
     ("ttn_kernel_timing", c_int, [c_void_p, c_int, c_double_p, c_int64_p, c_double_p, c_double_p, c_double_p]),

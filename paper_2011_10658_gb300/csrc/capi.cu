@@ -258,11 +258,20 @@ QED_API int ttn_set_mixed_tol(ttn_state* s, double mixed_tol) {
   return QED_OK;
 }
 
-QED_API int ttn_last_update(ttn_state* s, int32_t* iters_fp64, int32_t* iters_mixed, double* rel_residual) {
+QED_API int ttn_set_wait_limit(ttn_state* s, int64_t polls) {
+  if (!s) return fail(QED_EINVAL, "null state");
+  s->engine->wait_polls = polls < 0 ? -1 : polls;
+  return QED_OK;
+}
+
+QED_API int ttn_last_update(ttn_state* s, int32_t* iters_fp64, int32_t* iters_mixed, double* rel_residual,
+                            double* ritz_mixed, double* rel_residual_mixed) {
   if (!s) return fail(QED_EINVAL, "null state");
   if (iters_fp64) *iters_fp64 = s->engine->last_lanczos_iters;
   if (iters_mixed) *iters_mixed = s->engine->last_mixed_iters;
   if (rel_residual) *rel_residual = s->engine->last_residual;
+  if (ritz_mixed) *ritz_mixed = s->engine->last_mixed_ritz;
+  if (rel_residual_mixed) *rel_residual_mixed = s->engine->last_mixed_residual;
   return QED_OK;
 }
 
@@ -525,6 +534,7 @@ QED_API int ttn_load_tensors(ttn_state* s, const double* const* bufs, const int6
     std::vector<long long> sz(sizes, sizes + n_nodes);
     int rc = s->engine->load_tensors(bufs, sz.data(), n_nodes);
     if (rc == -1) return fail(QED_EINVAL, "tensor size mismatch");
+    if (rc == -5) return fail(QED_ENAN, "non-finite tensor entry");
     return engine_status(s->engine, rc);)
 }
 
@@ -650,9 +660,34 @@ QED_API int ttn_load(const qed_model* m, const char* path, void* cuda_stream, tt
       std::fclose(f);
       return fail(QED_EINVAL, "checkpoint parameters differ from the model");
     }
+    // node sizes the model implies at the stored bond dimension: every size
+    // read from the file must equal its expected value before anything is
+    // allocated for it (a corrupt size cannot trigger a huge allocation)
+    if (h.chi < 1 || h.chi > 4096) { std::fclose(f); return fail(QED_EINVAL, "checkpoint bond dimension out of range"); }
+    std::vector<int64_t> expect;
+    {
+      std::vector<qed::Sectors> bonds;
+      std::string err;
+      if (!qed::sector_table(p, h.chi, m->nodes, &bonds, &err)) { std::fclose(f); return fail(QED_EINVAL, err.c_str()); }
+      qed::Lattice lat{p.Lx, p.Ly, p.Lz};
+      for (const qed::TreeNode& nd : m->nodes) {
+        qed::Sectors legs[2];
+        for (int c = 0; c < 2; ++c)
+          legs[c] = nd.child_kind[c] == 0 ? qed::physical_sectors(lat.parity(nd.child[c])) : bonds[nd.child[c]];
+        const qed::Sectors& par = bonds[nd.index];
+        int64_t size = 0;
+        for (size_t ic = 0; ic < par.q.size(); ++ic)
+          for (size_t ia = 0; ia < legs[0].q.size(); ++ia) {
+            const int ib = legs[1].find(par.q[ic] - legs[0].q[ia]);
+            if (ib >= 0) size += (int64_t)legs[0].dim[ia] * legs[1].dim[ib] * par.dim[ic];
+          }
+        expect.push_back(size);
+      }
+    }
     std::vector<int64_t> sizes(h.n_nodes);
     bool ok = true;
-    for (int i = 0; ok && i < h.n_nodes; ++i) ok = read_all(f, &fnv, &sizes[i], 8) && sizes[i] >= 0 && sizes[i] < (1LL << 40);
+    for (int i = 0; ok && i < h.n_nodes; ++i) ok = read_all(f, &fnv, &sizes[i], 8) && sizes[i] == expect[i];
+    if (!ok) { std::fclose(f); return fail(QED_EINVAL, "checkpoint node sizes differ from the model's layout"); }
     std::vector<std::vector<double>> data(h.n_nodes);
     for (int i = 0; ok && i < h.n_nodes; ++i) {
       data[i].resize(sizes[i]);

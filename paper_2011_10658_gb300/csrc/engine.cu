@@ -11,6 +11,7 @@
 #include "engine.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -70,8 +71,23 @@ void Layout::build(const Sectors& a, const Sectors& b, const Sectors& c, int shi
   size = off;
 }
 
+// QED_FAIL_ALLOC_AFTER=n (read once per process): the allocation after the
+// first n succeeds as if cudaMalloc had run out of memory.  A host-side fake
+// of the failing call for tests of the QED_ENOMEM path.
+static long long fail_alloc_after() {
+  static const long long n = [] {
+    const char* v = std::getenv("QED_FAIL_ALLOC_AFTER");
+    return v ? std::atoll(v) : -1LL;
+  }();
+  return n;
+}
+
 void device_alloc(void** p, size_t bytes, const char* what) {
   *p = nullptr;
+  static std::atomic<long long> count{0};
+  const long long limit = fail_alloc_after();
+  if (limit >= 0 && count.fetch_add(1) >= limit)
+    throw DeviceAllocError(std::string(what) + ": out of memory (injected by QED_FAIL_ALLOC_AFTER)");
   const cudaError_t e = cudaMalloc(p, bytes == 0 ? 16 : bytes);
   if (e != cudaSuccess) {
     *p = nullptr;
@@ -611,7 +627,7 @@ Engine::Engine(const Params& p, int chi, uint64_t seed, int precision, cudaStrea
   grad_c_ = (double*)dalloc(nmax_ * sizeof(double));
   d_scal_ = (double*)dalloc(8192 * sizeof(double));
   d_partial_ = (double*)dalloc(304 * (kMaxKrylov + 2) * sizeof(double));
-  d_err_ = (int*)dalloc(4 * sizeof(int));   // [0] tensor-core wait flag, [1] thick-restart count
+  d_err_ = (int*)dalloc(4 * sizeof(int));   // [0] tensor-core wait flag, [1] thick-restart count, [2] non-finite flag
   if (!check(cudaStreamCreateWithFlags(&aux_, cudaStreamNonBlocking), "side stream")) throw std::runtime_error(err_);
   for (int i = 0; i <= kMaxKrylov; ++i) {
     cudaEventCreateWithFlags(&ev_iter_[i], cudaEventDisableTiming);
@@ -2030,7 +2046,7 @@ int Engine::apply_heff_mixed() {
   cudaEvent_t e0 = nullptr;
   if (profiling_) ev_begin(&e0);
   int rc = launch_tc_heff(elem, split, tc->d_tiles, (int)tc->tiles.size(), tc->d_outs, tc->d_chunks, tc->d_adds,
-                          tc->max_kpad, tc->max_npad, d_err_, stream_);
+                          tc->max_kpad, tc->max_npad, d_err_, stream_, wait_polls);
   if (rc) {
     err_ = "tensor-core H_eff: tile shape outside the supported range";
     return rc;
@@ -2313,12 +2329,16 @@ int Engine::optimize_node(int node, double tol, int max_krylov, SweepStats* st, 
   if (rc) return rc;
   double energy = 0, res = 0;
   int iters = 0, mixed_iters = 0;
+  last_mixed_ritz = std::nan("");
+  last_mixed_residual = std::nan("");
   if (mixed_node(node)) {
     cudaMemsetAsync(d_err_, 0, sizeof(int), stream_);
     // the low-precision phase aims a little below tol so that the FP64
     // check usually passes on its first product
     rc = lanczos(node, std::max(0.3 * tol, mixed_tol), max_krylov, true, 50, &energy, &res, &mixed_iters);
     if (rc) return rc;
+    last_mixed_ritz = energy;
+    last_mixed_residual = res / std::max(1e-300, std::fabs(energy));
     int herr = 0;
     cudaMemcpyAsync(&herr, d_err_, sizeof(int), cudaMemcpyDeviceToHost, stream_);
     if (!check(cudaStreamSynchronize(stream_), "mixed phase")) return -3;
@@ -2447,6 +2467,16 @@ int Engine::load_tensors(const double* const* host, const long long* sizes, int 
     if (sizes[i] != layout_[i].size || !host[i]) return -1;
   for (int i = 0; i < n; ++i)
     cudaMemcpyAsync(T_[i], host[i], sizes[i] * sizeof(double), cudaMemcpyHostToDevice, stream_);
+  // non-finite entries are looked for on the device, after the copies
+  cudaMemsetAsync(d_err_ + 2, 0, sizeof(int), stream_);
+  for (int i = 0; i < n; ++i) launch_check_finite(T_[i], sizes[i], d_err_ + 2, stream_);
+  int bad = 0;
+  cudaMemcpyAsync(&bad, d_err_ + 2, sizeof(int), cudaMemcpyDeviceToHost, stream_);
+  if (!check(cudaStreamSynchronize(stream_), "load")) return -3;
+  if (bad) {
+    err_ = "non-finite tensor entry";
+    return -5;
+  }
   tc_w_node_ = -1;
   for (const TreeNode& nd : nodes_)
     if (nd.parent >= 0) {
@@ -2561,11 +2591,6 @@ int Engine::noalloc_worklist(const double* x, double* y, KTile* tiles, int max_t
   *n_tiles = nt;
   *n_outs = no;
   *n_chunks = nc;
-  return 0;
-}
-
-long long Engine::matvec_flops_algorithmic(int node) {
-  (void)node;
   return 0;
 }
 

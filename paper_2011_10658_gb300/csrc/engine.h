@@ -245,11 +245,14 @@ class Engine {
   cudaStream_t stream() const { return stream_; }
   double* tensor(int n) { return T_[n]; }
   const std::string& error() const { return err_; }
-  long long matvec_flops_algorithmic(int node);
   long long device_bytes() const { return bytes_; }
   int last_lanczos_iters = 0;
   int last_mixed_iters = 0;
   double last_residual = 0.0;
+  // low-precision phase of the last mixed update: Ritz value and relative
+  // residual before the FP64 correction (NaN after an FP64 update)
+  double last_mixed_ritz = 0.0;
+  double last_mixed_residual = 0.0;
   // kernel timing (enabled by set_profiling): resolved on read
   void set_profiling(bool on);
   int kernel_timing(KernelTiming out[KC_COUNT]);
@@ -260,6 +263,8 @@ class Engine {
   void set_precision(int p);
   // mixed path tuning: residual target of the low-precision phase
   double mixed_tol = 0.0;
+  // bound of each mbarrier wait of the tensor-core kernels, in polls (< 0: default)
+  long long wait_polls = -1;
 
  private:
   Params p_;

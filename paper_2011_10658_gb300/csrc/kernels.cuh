@@ -97,6 +97,8 @@ void launch_fill_uniform(double* x, long long n, uint64_t seed, uint64_t start, 
 void launch_add_scaled(const double* x, double* y, long long n, double a, cudaStream_t s);
 void launch_zero(double* x, long long n, cudaStream_t s);
 void launch_to_float(const double* x, float* y, long long n, cudaStream_t s);
+// *flag = 1 if any of x[0..n) is NaN or infinite (flag untouched otherwise).
+void launch_check_finite(const double* x, long long n, int* flag, cudaStream_t s);
 void launch_to_double(const float* x, double* y, long long n, cudaStream_t s);
 
 // ---- small dense linear algebra (one CTA per matrix) ----
@@ -176,8 +178,10 @@ struct ConvJob {
 // W_lo]; three sub-products x_hi W_hi + x_hi W_lo + x_lo W_hi whose sum
 // carries about 21 bits (x_lo W_lo dropped).
 // err: device flag set to 1 if a wait timed out (results then invalid).
+// polls: bound of each mbarrier wait in polls (< 0: the default, 2^22).
 int launch_tc_heff(int elem, int split, const TcTile* tiles, int n_tiles, const TcOutput* outs,
-                   const TcChunk* chunks, const TcAdd* adds, int max_kpad, int max_npad, int* err, cudaStream_t s);
+                   const TcChunk* chunks, const TcAdd* adds, int max_kpad, int max_npad, int* err, cudaStream_t s,
+                   long long polls = -1);
 // mode 0: plain (BF16 or FP32 by elem); mode 1: split x rows [hi | lo] of
 // width 2 kpad; mode 2: split W rows [hi | lo] of width 2 kpad.  hi is
 // the value with its 13 low mantissa bits cleared (what the TF32 units read).

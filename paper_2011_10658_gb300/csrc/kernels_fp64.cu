@@ -299,6 +299,14 @@ __global__ void zero_kernel(double* __restrict__ x, long long n) {
     x[i] = 0.0;
 }
 
+// flag = 1 if some x[i] is NaN or infinite (exponent field all ones).
+__global__ void check_finite_kernel(const double* __restrict__ x, long long n, int* flag) {
+  bool bad = false;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    bad |= ((__double_as_longlong(x[i]) >> 52) & 0x7ff) == 0x7ff;
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(flag, 1);
+}
+
 __global__ void to_float_kernel(const double* __restrict__ x, float* __restrict__ y, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     y[i] = (float)x[i];
@@ -875,6 +883,12 @@ void launch_add_scaled(const double* x, double* y, long long n, double a, cudaSt
 void launch_zero(double* x, long long n, cudaStream_t s) {
   if (n <= 0) return;
   zero_kernel<<<grid_for(n), 256, 0, s>>>(x, n);
+  count_launches(1);
+}
+
+void launch_check_finite(const double* x, long long n, int* flag, cudaStream_t s) {
+  if (n <= 0) return;
+  check_finite_kernel<<<grid_for(n), 256, 0, s>>>(x, n, flag);
   count_launches(1);
 }
 

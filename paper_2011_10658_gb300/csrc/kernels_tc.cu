@@ -15,8 +15,10 @@
 //
 // One CTA = one 128-row tile of one output charge sector; 128 threads; two
 // shared-memory stages so the gather of term j+1 overlaps the MMAs of term
-// j.  Every mbarrier wait is bounded; a timeout sets *err and the CTA
-// drains, frees its TMEM and returns.
+// j.  Every mbarrier wait is bounded (polls, a launch argument); a timeout
+// sets *err, and the CTA then drains its MMAs through a commit to a fresh
+// barrier (waited on with the default bound, so the MMAs still in flight
+// finish before TMEM is read or freed), frees its TMEM and returns.
 #include <algorithm>
 #include <cuda_bf16.h>
 
@@ -29,7 +31,7 @@ namespace qed {
 namespace {
 
 constexpr int TC_THREADS = 128;
-constexpr long long kWaitPolls = 1LL << 22;
+constexpr long long kWaitPolls = 1LL << 22;   // default bound of one mbarrier wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -50,8 +52,8 @@ __device__ __forceinline__ uint32_t core_off(int r, int q, int kchunks) {
   return (uint32_t)(((r >> 3) * kchunks + q) * 128 + (r & 7) * 16);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
-  for (long long it = 0; it < kWaitPolls; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, long long polls = kWaitPolls) {
+  for (long long it = 0; it < polls; ++it) {
     uint32_t done;
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
@@ -81,10 +83,10 @@ __global__ void __launch_bounds__(TC_THREADS) tc_heff_kernel(const TcTile* __res
                                                               const TcOutput* __restrict__ outs,
                                                               const TcChunk* __restrict__ chunks,
                                                               const TcAdd* __restrict__ adds, int a_bytes,
-                                                              int b_bytes, int* err) {
+                                                              int b_bytes, int* err, long long polls) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ uint32_t tmem_slot;
-  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t mbar[3];   // two stages, one drain
   __shared__ int s_fail;
   const TcTile tile = tiles[blockIdx.x];
   const TcOutput out = outs[tile.out];
@@ -101,6 +103,7 @@ __global__ void __launch_bounds__(TC_THREADS) tc_heff_kernel(const TcTile* __res
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[2])), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;");
     s_fail = 0;
   }
@@ -175,16 +178,22 @@ __global__ void __launch_bounds__(TC_THREADS) tc_heff_kernel(const TcTile* __res
       uses[b] += 1;
       if (j + 1 < nchunks) {
         const int nb = b ^ 1;
-        if (uses[nb] > 0 && !mbar_wait(smem_u32(&mbar[nb]), (uses[nb] - 1) & 1)) s_fail = 1;
+        if (uses[nb] > 0 && !mbar_wait(smem_u32(&mbar[nb]), (uses[nb] - 1) & 1, polls)) s_fail = 1;
         load_chunk(out.chunk_begin + j + 1, nb);
         asm volatile("fence.proxy.async.shared::cta;");
         __syncthreads();
       }
     }
-    const int lb = (nchunks - 1) & 1;
-    if (!mbar_wait(smem_u32(&mbar[lb]), (uses[lb] - 1) & 1)) {
+    // drain: one more commit from the issuing thread arrives on mbar[2] once
+    // every MMA it issued has completed (whatever happened to the stage
+    // barriers); the wait uses the caller's bound, and after a timeout the
+    // default bound, so TMEM is read and freed only after the MMAs are done
+    if (tid == 0)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&mbar[2])));
+    if (!mbar_wait(smem_u32(&mbar[2]), 0, polls)) {
       s_fail = 1;
-      mbar_wait(smem_u32(&mbar[lb]), (uses[lb] - 1) & 1);   // drain once more before freeing TMEM
+      mbar_wait(smem_u32(&mbar[2]), 0);
     }
     asm volatile("tcgen05.fence::after_thread_sync;");
   }
@@ -262,8 +271,10 @@ __global__ void __launch_bounds__(256) convert_kernel(const ConvJob* __restrict_
 }  // namespace
 
 int launch_tc_heff(int elem, int split, const TcTile* tiles, int n_tiles, const TcOutput* outs,
-                   const TcChunk* chunks, const TcAdd* adds, int max_kpad, int max_npad, int* err, cudaStream_t s) {
+                   const TcChunk* chunks, const TcAdd* adds, int max_kpad, int max_npad, int* err, cudaStream_t s,
+                   long long polls) {
   if (n_tiles <= 0) return 0;
+  if (polls < 0) polls = kWaitPolls;
   const int a_bytes = 128 * max_kpad * elem;
   const int b_bytes = max_npad * max_kpad * elem;
   const int smem = 2 * (a_bytes + b_bytes);
@@ -271,15 +282,15 @@ int launch_tc_heff(int elem, int split, const TcTile* tiles, int n_tiles, const 
   if (split && elem != 4) return -7;
   if (elem == 2) {
     cudaFuncSetAttribute(tc_heff_kernel<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    tc_heff_kernel<2, false><<<n_tiles, TC_THREADS, smem, s>>>(tiles, outs, chunks, adds, a_bytes, b_bytes, err);
+    tc_heff_kernel<2, false><<<n_tiles, TC_THREADS, smem, s>>>(tiles, outs, chunks, adds, a_bytes, b_bytes, err, polls);
     count_launches(1);
   } else if (!split) {
     cudaFuncSetAttribute(tc_heff_kernel<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    tc_heff_kernel<4, false><<<n_tiles, TC_THREADS, smem, s>>>(tiles, outs, chunks, adds, a_bytes, b_bytes, err);
+    tc_heff_kernel<4, false><<<n_tiles, TC_THREADS, smem, s>>>(tiles, outs, chunks, adds, a_bytes, b_bytes, err, polls);
     count_launches(1);
   } else {
     cudaFuncSetAttribute(tc_heff_kernel<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    tc_heff_kernel<4, true><<<n_tiles, TC_THREADS, smem, s>>>(tiles, outs, chunks, adds, a_bytes, b_bytes, err);
+    tc_heff_kernel<4, true><<<n_tiles, TC_THREADS, smem, s>>>(tiles, outs, chunks, adds, a_bytes, b_bytes, err, polls);
     count_launches(1);
   }
   return 0;

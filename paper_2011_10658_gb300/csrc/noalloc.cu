@@ -75,10 +75,15 @@ QED_API int ttn_apply_heff_device_noalloc(ttn_state* s, const double* x_device, 
                                (int)(kOutBytes / sizeof(qed::KOutput)), chunks,
                                (int)(kChunkBytes / sizeof(qed::KChunk)), &nt, &no, &nc);
   if (rc == -2) return fail(QED_EUNSUPPORTED, "work list exceeds the 4 MiB scratch array");
-  if (rc) return fail(QED_EUNSUPPORTED, "centre must be a bottom node reached by ttn_move_center or a sweep");
+  // the engine names what is missing: a centre that is not a bottom node, or
+  // a row map / environment operator not built yet at this centre
+  if (rc) return fail(QED_EUNSUPPORTED, e->error().c_str());
   cudaStream_t st = e->stream();
   // the whole work list is rewritten every call; nothing must start at zero
-  // (every output tile is stored, not accumulated, and no partial sums are used)
+  // (every output tile is stored, not accumulated, and no partial sums are used).
+  // g_host is pageable: a host-to-device cudaMemcpyAsync from pageable memory
+  // first waits for the work already queued on the stream and returns once
+  // the host buffer has been read, so the next call may rewrite g_host.
   if (cudaMemcpyAsync(dbase, tiles, nt * sizeof(qed::KTile), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(dbase + kTileBytes, outs, no * sizeof(qed::KOutput), cudaMemcpyHostToDevice, st) !=
           cudaSuccess ||
