@@ -10,13 +10,21 @@ operator updates, Lanczos with H_eff products, tensor updates).
 
 value = algorithmic H_eff x flops of every product in the timed sweeps /
 timed wall time (TFLOP/s); the same sweeps' seconds are in ms_per_step.
-Precision (default tf32x3): bottom-node products on tcgen05 with TF32
-hi/lo operand splitting and FP32 accumulation, upper nodes in FP32; Lanczos
-vectors, QR, operator updates and the final energy of each update in FP64.
+Precision (default tf32x3): H_eff x products on tcgen05 with split-TF32
+operands and FP32 accumulation, then the FP64 residual correction; Lanczos
+vectors, QR and the final energy of each update in FP64.
+
+Extra keys (rank 0, one GPU): per-class kernel times with each class's rate
+against its own measured peak; the dominant class's roofline; in-run peak
+probes (cuBLAS FP64 / FP32 / TF32 / BF16 GEMMs); node updates repeated from
+identical states in FP64 and in the mixed precision (energy difference and
+speed-up at matched accuracy); the TF32 and BF16 arms and the g^2 scan
+{0.5, 2, 4} of the precision configuration; the FP64 path's sweeps and the
+time each path needs to reach a common energy.
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 workload (H_eff x at bottom node 0 with synthetic environment operators of
-the right shapes) and reports it in the same unit.
+the right shapes; algorithmic flops counted by the oracle itself).
 """
 import argparse
 import json
@@ -41,20 +49,34 @@ G2 = 1.0
 Q = 0
 TOL = 1e-6
 KRYLOV = 64
+PRODUCT_CLASSES = ("tc_heff", "heff_simt_bottom", "heff_simt_upper")
+ALL_CLASSES = ("tc_heff", "heff_simt_bottom", "heff_simt_upper", "move", "lanczos", "move_qr", "move_ops")
 
 
-def workload_name(prec):
-    return (f"4x4x4 open-boundary lattice QED (64 dressed sites, d=267), t=m=1, g2=1 (ge2=1, cB=0.5, nu=10), "
-            f"Q=0, TTN chi=64 U(1) blocks, seed 1, Lanczos tol 1e-6, Krylov 64, precision {prec}")
+def workload_name(prec, g2=G2):
+    c = workloads.qed_couplings(g2)
+    return (f"4x4x4 open-boundary lattice QED (64 dressed sites, d=267), t=m=1, g2={g2:g} (ge2={c['ge2']:g}, "
+            f"cB={c['cB']:g}, nu={c['nu']:g}), Q=0, TTN chi=64 U(1) blocks, seed 1, Lanczos tol 1e-6, Krylov 64, "
+            f"precision {prec}")
 
 
-def peaks():
+def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            d = json.load(f)
-        return d, "measured"
+            return json.load(f), "measured"
     except Exception:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
 
 
 class ClockSampler:
@@ -128,19 +150,46 @@ def traffic_from_profile(kernel_src):
         return None
 
 
+# ---------------------------------------------------------------- peaks
+def probe_peaks(device):
+    """Dense GEMM rates of this GPU measured now (cuBLAS through torch):
+    FP64, FP32 with TF32 off (SIMT), TF32 and BF16, best of 3 after a
+    warm-up, CUDA events; the denominators of the per-class fractions."""
+    import torch
+    out = {}
+    old = torch.backends.cuda.matmul.allow_tf32
+    try:
+        for name, dtype, n, tf32 in (("fp64", torch.float64, 4096, False), ("fp32_simt", torch.float32, 8192, False),
+                                     ("tf32", torch.float32, 8192, True), ("bf16", torch.bfloat16, 8192, False)):
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            a = torch.randn(n, n, device=device, dtype=dtype)
+            b = torch.randn(n, n, device=device, dtype=dtype)
+            c = a @ b
+            best = 1e30
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                c = a @ b
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            out[name] = 2.0 * n ** 3 / (best * 1e-3) / 1e12
+            del a, b, c
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = old
+    torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------------- oracle sample
-def oracle_sample(n_matvecs=None, budget_s=20.0):
-    """Time the FP64 oracle's H_eff x at bottom node 0 of the workload.
-    Environment operators are random matrices of the right shapes (the
-    oracle's cost depends on shapes only).  Returns (seconds per matvec,
-    matvecs timed, cores)."""
+def _oracle_with_random_env(node):
+    """Oracle TTN of the workload with synthetic environment operators of
+    the right shapes at `node` (the oracle's cost depends on shapes only)."""
     import numpy as np
     from oracle import model as omodel
     from oracle import ttn as ottn
     c = workloads.qed_couplings(G2)
-    p = omodel.Params(*L, Q=Q, **c)
-    ref = ottn.TTN(p, CHI, SEED, build_ops=False)
-    node = 0
+    ref = ottn.TTN(omodel.Params(*L, Q=Q, **c), CHI, SEED, build_ops=False)
     rng = np.random.default_rng(0)
     dim = ref.T[node].shape[2]
     env = {}
@@ -150,6 +199,23 @@ def oracle_sample(n_matvecs=None, budget_s=20.0):
     H = rng.standard_normal((dim, dim))
     env["H"] = H + H.T
     ref.down[node] = env
+    if ref.nodes[node].children[0][0] == "node":
+        for kind, cid in ref.nodes[node].children:
+            d = ref.T[cid].shape[2]
+            ops = {k: rng.standard_normal((d, d)) for k, tm in enumerate(ref.terms)
+                   if ref._crosses(tm, ref.region[cid])}
+            Hc = rng.standard_normal((d, d))
+            ops["H"] = Hc + Hc.T
+            ref.up[cid] = ops
+    return ref
+
+
+def oracle_sample(n_matvecs=None, budget_s=20.0, node=0):
+    """Time the FP64 oracle's H_eff x at `node` of the workload.  Returns
+    (seconds per product, products timed, threads, flops per product); the
+    flops are the oracle's own count (bottom nodes only, else None)."""
+    from oracle import ttn as ottn
+    ref = _oracle_with_random_env(node)
     terms = ref.heff_terms(node)
     X = ref.T[node]
     ref.heff_apply(node, X, terms)   # warm
@@ -164,27 +230,25 @@ def oracle_sample(n_matvecs=None, budget_s=20.0):
         if n_matvecs is None and time.time() - t_start > budget_s:
             break
     try:
-        import numpy as _np
         cores = len(os.sched_getaffinity(0))
     except Exception:
         cores = os.cpu_count()
-    return float(sum(times) / len(times)), len(times), cores
+    threads = int(os.environ.get("OMP_NUM_THREADS", cores))
+    flops = ottn.bottom_heff_flops(ref, node) if ref.nodes[node].children[0][0] == "site" else None
+    return float(sum(times) / len(times)), len(times), threads, flops
 
 
-def node0_flops():
-    """Algorithmic flops of one H_eff x at bottom node 0 (the same count the
-    native profiler reports), from a short native run."""
-    import paper_2011_10658_gb300 as q
-    c = workloads.qed_couplings(G2)
-    s = q.TTN(q.Model(*L, Q=Q, **c), CHI, seed=SEED, precision="tf32x3")
-    s.move_center(0)
-    s.set_profiling(True)
-    s.reset_timing()
-    import numpy as np
-    s.apply_heff(np.ones(s.node_size(0)))
-    t = s.kernel_timing("tc_heff")
-    s.close()
-    return t["flops_alg"] / max(1, t["launches"])
+def oracle_single_thread(n_matvecs=2):
+    """The same sample with one BLAS thread, in a child process."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json, bench; t, n, th, f = bench.oracle_sample(n_matvecs=%d); "
+            "print(json.dumps({'t': t, 'n': n, 'flops': f}))" % n_matvecs)
+    try:
+        out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                             timeout=900)
+        return json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception as exc:
+        return {"error": str(exc)[:200]}
 
 
 def run_reference(args):
@@ -193,25 +257,22 @@ def run_reference(args):
         return
     per_step = []
     flops = None
-    try:
-        import torch
-        if torch.cuda.is_available():
-            flops = node0_flops()
-    except Exception:
-        flops = None
+    threads = None
     for i in range(args.warmup + args.steps):
-        t, n, cores = oracle_sample(n_matvecs=2)
+        t, n, threads, flops = oracle_sample(n_matvecs=2)
         if i >= args.warmup:
             per_step.append(t * n)
     sec_per_mv = sum(per_step) / (2 * len(per_step))
-    value = (flops / sec_per_mv / 1e12) if flops else None
+    value = flops / sec_per_mv / 1e12
     sample = (f"FP64 NumPy/SciPy oracle, H_eff x at bottom node 0 of the 4x4x4 chi=64 workload (environment "
-              f"operators random, same shapes), 2 products per step, {sec_per_mv:.3f} s per product")
+              f"operators random, same shapes), 2 products per step, {sec_per_mv:.3f} s per product, "
+              f"{flops / 1e9:.3f} GFLOP algorithmic per product (oracle's own count); CPU {cpu_model()}")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(per_step) / len(per_step),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": workload_name("fp64 CPU oracle")},
-            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -235,6 +296,33 @@ def reduce_over_ranks(elapsed_ms, flops, device):
     return mx[0].item(), sm[1].item()
 
 
+def class_table(kt, elapsed_ms, peaks, precision):
+    """Disjoint kernel classes of the timed sweeps with their share of the
+    step and their rate against their own peak and the peak the hot-path
+    table assigns (tensor cores for every contraction)."""
+    lanczos_vec = kt["lanczos"]["ms"] - sum(kt[k]["ms"] for k in PRODUCT_CLASSES)
+    rows = {}
+    own = {"tc_heff": ("bf16" if precision == "bf16" else "tf32"),
+           "heff_simt_bottom": "fp64",
+           "heff_simt_upper": ("fp64" if precision == "fp64" else "fp32_simt"),
+           "move_ops": "fp64"}
+    for k in ("tc_heff", "heff_simt_bottom", "heff_simt_upper", "move_ops", "move_qr"):
+        v = kt[k]
+        r = {"ms": v["ms"], "launches": v["launches"], "share_of_step": v["ms"] / elapsed_ms}
+        if v["flops_alg"] > 0 and v["ms"] > 0:
+            rate = v["flops_alg"] / (v["ms"] * 1e-3) / 1e12
+            r["tflops_alg"] = rate
+            if k in own:
+                r["own_peak"] = {"dtype": own[k], "tflops": peaks[own[k]], "frac": rate / peaks[own[k]]}
+                tp = "bf16" if precision == "bf16" else "tf32"
+                r["tensor_peak"] = {"dtype": tp, "tflops": peaks[tp], "frac": rate / peaks[tp]}
+        rows[k] = r
+    rows["lanczos_vectors"] = {"ms": lanczos_vec, "share_of_step": lanczos_vec / elapsed_ms,
+                               "note": "Lanczos time minus its products: FP64 dots, reorthogonalisation, "
+                                       "tridiagonal solve, host checks"}
+    return rows
+
+
 def run_native(args):
     import numpy as np
     import torch
@@ -248,19 +336,24 @@ def run_native(args):
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
+    props = torch.cuda.get_device_properties(local)
     c = workloads.qed_couplings(G2)
     model = q.Model(*L, Q=Q, **c)
     # replicas only: rank r runs an independent problem from seed SEED + r
     s = q.TTN(model, CHI, seed=replica_seed(rank), precision=args.precision, stream=stream.cuda_stream)
     s.set_profiling(True)
-    energies = []
+    energies, warm_s = [], []
 
     def barrier():
         if world > 1:
             dist.barrier()
 
     for _ in range(args.warmup):
+        torch.cuda.synchronize()
+        t0 = time.time()
         st = s.sweep(1, tol=TOL, max_krylov=KRYLOV, allow_noconv=True)
+        torch.cuda.synchronize()
+        warm_s.append(time.time() - t0)
         energies.append(st["energy"])
     s.reset_timing()
     sampler = ClockSampler(local)
@@ -284,53 +377,45 @@ def run_native(args):
     elapsed_ms = ev0.elapsed_time(ev1)
     launches = q.launch_count() - launches0
     clocks = sampler.stop()
-    kt = {k: s.kernel_timing(k) for k in ("tc_heff", "heff_simt_bottom", "heff_simt_upper", "move", "lanczos", "move_qr", "move_ops")}
-    flops = sum(kt[k]["flops_alg"] for k in ("tc_heff", "heff_simt_bottom", "heff_simt_upper"))
+    kt = {k: s.kernel_timing(k) for k in ALL_CLASSES}
+    flops = sum(kt[k]["flops_alg"] for k in PRODUCT_CLASSES)
     if world > 1:
         elapsed_ms, flops = reduce_over_ranks(elapsed_ms, flops, "cuda")
     value = flops / (elapsed_ms * 1e-3) / 1e12
 
-    # dominant kernel roofline (kernel classes only, not whole phases)
-    dom = max(("tc_heff", "heff_simt_bottom", "heff_simt_upper"), key=lambda k: kt[k]["ms"])
+    pk, src = measured_peaks()
+    peaks = {"bf16": pk["bf16_tflops_sustained"]}
+    probed = None
+    if rank == 0 and not args.no_probe:
+        probed = probe_peaks("cuda")
+        peaks.update({k: v for k, v in probed.items() if k != "bf16"})
+    else:
+        # nominal ratios to the measured BF16 rate when the probes are skipped
+        peaks.update({"tf32": peaks["bf16"] * 1.1 / 2.25, "fp64": 1.25,
+                      "fp32_simt": props.multi_processor_count * 128 * 2 * pk.get("sm_max_mhz", 2070.0) / 1e6})
+    classes = class_table(kt, elapsed_ms, peaks, args.precision)
+
+    # roofline of the class with the most kernel time among the flop-counted
+    # contraction classes (products and operator updates)
+    dom = max(("tc_heff", "heff_simt_bottom", "heff_simt_upper", "move_ops"), key=lambda k: kt[k]["ms"])
     d = kt[dom]
-    pk, src = peaks()
     per_launch_ms = d["ms"] / max(1, d["launches"])
     achieved = d["flops_alg"] / max(1, d["launches"]) / (per_launch_ms * 1e-3) / 1e12
+    tensor_dtype = "bf16" if args.precision == "bf16" else "tf32"
+    peak = peaks[tensor_dtype]
+    traffic = None
     if dom == "tc_heff":
-        # TF32 tensor rate = BF16 rate x nominal ratio (1.1 / 2.25 PFLOP/s dense); kernel timed inside a long step
-        peak = pk["bf16_tflops_sustained"] * (1.1 / 2.25)
-        bound, peak_note = "tensor", f"TF32 dense = {src} sustained BF16 {pk['bf16_tflops_sustained']} x 1.1/2.25"
         traffic = traffic_from_profile(os.path.join(ROOT, "paper_2011_10658_gb300", "csrc", "kernels_tc.cu"))
-    elif dom == "heff_simt_bottom" or args.precision == "fp64":
-        # FP64 products: GB300's FP64 rate (nominal 1.25 TFLOP/s)
-        peak, bound, peak_note, traffic = 1.25, "alu", "FP64 SIMT, nominal 1.25 TFLOP/s", None
-    else:
-        # FP32 SIMT: 152 SMs x 128 lanes x 2 flops x max SM clock
-        peak = 152 * 128 * 2 * (pk.get("sm_max_mhz", 2070.0) * 1e6) / 1e12
-        bound, peak_note, traffic = "alu", "FP32 SIMT 152 x 128 x 2 x 2070 MHz", None
-    # every product class and the FP64 operator updates against their own peaks
-    # (context for the dominant-class roofline above; FP64 SIMT peak from the
-    # nominal 1.25 TFLOP/s of this part, FP32 SIMT 152 x 128 x 2 x max clock)
-    fp64_peak = 1.25
-    fp32_peak = 152 * 128 * 2 * (pk.get("sm_max_mhz", 2070.0) * 1e6) / 1e12
-    tf32_peak = pk["bf16_tflops_sustained"] * (1.1 / 2.25)
-    class_rates = {}
-    for k, pkv, unit_note in (("tc_heff", tf32_peak, "TF32 tensor (measured BF16 sustained x 1.1/2.25)"),
-                              ("heff_simt_bottom", fp64_peak, "FP64 SIMT (nominal)"),
-                              ("heff_simt_upper", fp64_peak if args.precision == "fp64" else fp32_peak,
-                               "FP64 SIMT (nominal)" if args.precision == "fp64" else "FP32 SIMT (mostly)"),
-                              ("move_ops", fp64_peak, "FP64 SIMT (nominal)")):
-        v = kt[k]
-        if v["ms"] > 0 and v["flops_alg"] > 0:
-            r = v["flops_alg"] / (v["ms"] * 1e-3) / 1e12
-            class_rates[k] = {"tflops": r, "peak": pkv, "frac": r / pkv, "peak_source": unit_note,
-                              "ms": v["ms"], "launches": v["launches"]}
-    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_note,
+    roofline = {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_source": (f"{tensor_dtype} dense GEMM measured in this run (cuBLAS)" if probed else
+                                f"{src} BF16 sustained x nominal ratio"),
+                "own_dtype_frac": classes.get(dom, {}).get("own_peak"),
                 "launches": d["launches"], "ms_per_launch": per_launch_ms,
                 "algorithmic_flops_per_launch": d["flops_alg"] / max(1, d["launches"]),
                 "executed_flops_per_launch": d["flops_exec"] / max(1, d["launches"]),
                 "share_of_step": d["ms"] / elapsed_ms}
+    largest = max(classes, key=lambda k: classes[k]["ms"])
 
     # end to end through the public API with host buffers: tensors in from
     # pinned host memory, sweep, tensors and energy back to the host
@@ -339,7 +424,6 @@ def run_native(args):
     for i in range(nn):
         host[i].numpy()[:] = s.node_export(i)
     h2d = sum(h.numel() * 8 for h in host)
-    e2e_flops = 0.0
     s.reset_timing()
     torch.cuda.synchronize()
     t0 = time.time()
@@ -348,57 +432,33 @@ def run_native(args):
         st = s.sweep(1, tol=TOL, max_krylov=KRYLOV, allow_noconv=True)
         for i in range(nn):
             host[i].numpy()[:] = s.node_export(i)
-        e_back = st["energy"]
     torch.cuda.synchronize()
     e2e_s = time.time() - t0
-    kt2 = {k: s.kernel_timing(k) for k in ("tc_heff", "heff_simt_bottom", "heff_simt_upper")}
+    kt2 = {k: s.kernel_timing(k) for k in PRODUCT_CLASSES}
     e2e_flops = sum(v["flops_alg"] for v in kt2.values())
     e2e = {"value": e2e_flops / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": h2d + 8, "seconds_per_step": e2e_s / args.steps}
 
-    # per-update |dE|/|E| on identical H_eff: the same node update from the
-    # same state, once with FP64 products and once in the state's precision
-    per_update = None
-    if args.precision != "fp64" and rank == 0:
-        rows = []
-        for node in (0, 1, 16, 31, 32, 48, 56, 62):
-            s.move_center(node)
-            t0 = s.node_export(node)
-            s.set_precision("fp64")
-            e64 = s.optimize_node(node, tol=TOL, max_krylov=KRYLOV)
-            s.node_import(node, t0)
-            s.set_precision(args.precision)
-            em = s.optimize_node(node, tol=TOL, max_krylov=KRYLOV)
-            rows.append({"node": node, "e_fp64": e64, "e_mixed": em, "rel_dE": abs(em - e64) / abs(e64)})
-        per_update = {"nodes": rows, "max_rel_dE": max(r["rel_dE"] for r in rows)}
-
-    # FP64 GPU path on the same workload and sweeps for |dE|/|E|
-    compare = None
-    if args.compare_fp64 and args.precision != "fp64" and rank == 0:
-        r = q.TTN(model, CHI, seed=replica_seed(rank), precision="fp64", stream=stream.cuda_stream)
-        e64, t64 = [], []
-        for _ in range(args.warmup + args.steps):
-            torch.cuda.synchronize()
-            t0 = time.time()
-            e64.append(r.sweep(1, tol=TOL, max_krylov=KRYLOV, allow_noconv=True)["energy"])
-            torch.cuda.synchronize()
-            t64.append(time.time() - t0)
-        rel = [abs(a - b) / abs(b) for a, b in zip(energies, e64)]
-        # the same sweeps as the timed mixed ones (after the warm-up sweeps)
-        fp64_timed = sum(t64[args.warmup:]) / max(1, args.steps)
-        compare = {"energies_mixed": energies, "energies_fp64": e64, "max_rel_dE": max(rel),
-                   "fp64_seconds_per_sweep_each": t64, "fp64_seconds_per_timed_sweep": fp64_timed,
-                   "speedup_same_sweeps": fp64_timed / (elapsed_ms / args.steps / 1e3)}
-        r.close()
+    extra = {}
+    if rank == 0 and world == 1:
+        extra = run_extras(args, q, model, s, stream, energies, warm_s, elapsed_ms / args.steps / 1e3)
+    s.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t_mv, n_mv, cores = oracle_sample(budget_s=args.cpu_seconds)
-        f0 = node0_flops()
-        cpu = {"value": f0 / t_mv / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-               "sample": (f"FP64 NumPy/SciPy oracle: {n_mv} H_eff x products at bottom node 0 of this workload "
-                          f"(random environment operators of the same shapes), {t_mv:.3f} s each; "
-                          f"{f0 / 1e9:.2f} GFLOP algorithmic per product")}
+        t_mv, n_mv, threads, f0 = oracle_sample(budget_s=args.cpu_seconds)
+        one = oracle_single_thread()
+        sample = (f"FP64 NumPy/SciPy oracle: {n_mv} H_eff x products at bottom node 0 of this workload "
+                  f"(random environment operators of the same shapes), {t_mv:.3f} s each with {threads} threads; "
+                  f"{f0 / 1e9:.3f} GFLOP algorithmic per product (oracle's own count); CPU {cpu_model()}")
+        cpu = {"value": f0 / t_mv / 1e12, "unit": "TFLOP/s", "cores": threads, "kind": "oracle", "sample": sample,
+               "single_thread": ({"seconds_per_product": one["t"], "tflops": f0 / one["t"] / 1e12}
+                                 if "t" in one else one)}
+        # products of one sweep at the oracle's rate (a lower bound of an
+        # oracle sweep: operator updates and the eigensolver's own work not
+        # included), extrapolated from the timed bottom-node products
+        per_sweep = value * (elapsed_ms / args.steps * 1e-3) * 1e12
+        cpu["sweep_seconds_extrapolated"] = per_sweep / (f0 / t_mv)
 
     if rank == 0:
         total_mv = sum(st["matvecs"] for st in stats)
@@ -412,14 +472,110 @@ def run_native(args):
             "sweep_s": elapsed_ms / args.steps / 1e3,
             "energy": energies[-1],
             "matvecs_per_sweep": total_mv / args.steps, "mixed_matvecs_per_sweep": mixed_mv / args.steps,
-            "roofline": roofline, "class_rates": class_rates, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": launches, "kernels": kt, "per_update_vs_fp64": per_update,
-            "fp64_trajectory_comparison": compare,
+            "not_converged": sum(st["not_converged"] for st in stats),
+            "node_updates": sum(st["node_updates"] for st in stats),
+            "max_rel_residual": max(st["max_rel_residual"] for st in stats),
+            "roofline": roofline, "largest_class": largest, "classes": classes, "peaks_tflops": peaks,
+            "sm_count": props.multi_processor_count,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": launches, "launches_per_sweep": launches / args.steps, "kernels": kt,
         }
+        line.update(extra)
         print(json.dumps(line), flush=True)
-    s.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def _timed_update(q, s, node, precision, t0, stream):
+    """One node update from tensor t0 in `precision`, CUDA-event timed."""
+    import torch
+    s.set_precision(precision)
+    s.node_import(node, t0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    e = s.optimize_node(node, tol=TOL, max_krylov=KRYLOV)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e, e0.elapsed_time(e1), s.last_update()
+
+
+def run_extras(args, q, model, s, stream, energies, warm_s, sweep_s):
+    """Matched-accuracy comparison with the FP64 path and the precision
+    arms of the precision configuration (rank 0, one GPU)."""
+    import torch
+    out = {}
+    # per-update: identical state and H_eff, FP64 vs mixed, both to TOL
+    rows = []
+    if args.precision != "fp64":
+        for node in (0, 1, 16, 31, 32, 48, 56, 62):
+            s.move_center(node)
+            t0 = s.node_export(node)
+            e64, ms64, lu64 = _timed_update(q, s, node, "fp64", t0, stream)
+            em, msm, lum = _timed_update(q, s, node, args.precision, t0, stream)
+            rows.append({"node": node, "e_fp64": e64, "e_mixed": em, "rel_dE": abs(em - e64) / abs(e64),
+                         "ritz_low_precision": lum["ritz_mixed"],
+                         "rel_dE_low_precision": abs(lum["ritz_mixed"] - e64) / abs(e64),
+                         "ms_fp64": ms64, "ms_mixed": msm, "iters_fp64": lu64["iters_fp64"],
+                         "iters_mixed": lum["iters_mixed"], "iters_correction": lum["iters_fp64"]})
+        s.set_precision(args.precision)
+        out["per_update_vs_fp64"] = {
+            "nodes": rows, "max_rel_dE": max(r["rel_dE"] for r in rows),
+            "speedup_matched_accuracy": sum(r["ms_fp64"] for r in rows) / sum(r["ms_mixed"] for r in rows),
+            "note": "the same node updates from identical states, both to relative residual 1e-6"}
+    if args.arms:
+        arms = {}
+        for prec, g2 in (("tf32", 1.0), ("bf16", 1.0), ("tf32x3", 0.5), ("tf32x3", 2.0), ("tf32x3", 4.0)):
+            r = q.TTN(q.Model(*L, Q=Q, **workloads.qed_couplings(g2)), CHI, seed=SEED, precision=prec,
+                      stream=stream.cuda_stream)
+            r.set_profiling(True)
+            for _ in range(3):
+                r.sweep(1, tol=TOL, max_krylov=KRYLOV, allow_noconv=True)
+            r.reset_timing()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = r.sweep(1, tol=TOL, max_krylov=KRYLOV, allow_noconv=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            f = sum(r.kernel_timing(k)["flops_alg"] for k in PRODUCT_CLASSES)
+            arms[f"{prec}_g2={g2:g}"] = {"sweep_s": ms / 1e3, "tflops": f / (ms * 1e-3) / 1e12,
+                                         "energy_after_4_sweeps": st["energy"], "not_converged": st["not_converged"],
+                                         "max_rel_residual": st["max_rel_residual"]}
+            r.close()
+        out["precision_arms"] = arms
+    if args.compare_fp64 and args.precision != "fp64":
+        # the FP64 path from the same seed: energies after every sweep and the
+        # time each path needs to reach a common energy (the higher of the two
+        # final energies)
+        r = q.TTN(model, CHI, seed=SEED, precision="fp64", stream=stream.cuda_stream)
+        e64, t64 = [], []
+        for _ in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            t0 = time.time()
+            e64.append(r.sweep(1, tol=TOL, max_krylov=KRYLOV, allow_noconv=True)["energy"])
+            torch.cuda.synchronize()
+            t64.append(time.time() - t0)
+        r.close()
+        tm = list(warm_s) + [sweep_s] * (len(energies) - len(warm_s))
+        target = max(e64[-1], energies[-1])
+
+        def time_to(es, ts):
+            acc = 0.0
+            for e, t in zip(es, ts):
+                acc += t
+                if e <= target + 1e-12 * abs(target):
+                    return acc
+            return None
+
+        t_m, t_f = time_to(energies, tm), time_to(e64, t64)
+        out["fp64_trajectory_comparison"] = {
+            "energies_mixed": energies, "energies_fp64": e64, "seconds_mixed_each": tm, "seconds_fp64_each": t64,
+            "end_rel_dE": abs(energies[-1] - e64[-1]) / abs(e64[-1]), "common_target_energy": target,
+            "seconds_to_target_mixed": t_m, "seconds_to_target_fp64": t_f,
+            "speedup_to_common_energy": (t_f / t_m) if (t_m and t_f) else None}
+    return out
 
 
 def run_heff_only(args):
@@ -440,6 +596,8 @@ def run_heff_only(args):
     for _ in range(args.warmup):
         s.apply_heff_device(x.data_ptr(), y.data_ptr(), n)
     torch.cuda.synchronize()
+    s.set_profiling(True)
+    s.reset_timing()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
@@ -447,12 +605,16 @@ def run_heff_only(args):
     ev1.record(stream)
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / max(1, args.steps)
+    kt = {k: s.kernel_timing(k) for k in PRODUCT_CLASSES}
+    s.set_profiling(False)
     torch.cuda.profiler.start()
     s.apply_heff_device(x.data_ptr(), y.data_ptr(), n)
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
+    flops = sum(v["flops_alg"] for v in kt.values()) / max(1, args.steps)
     print(json.dumps({"mode": "heff", "node": args.node, "size": n, "precision": args.precision,
-                      "ms_per_product": ms, "products_timed": args.steps,
+                      "ms_per_product": ms, "products_timed": args.steps, "flops_alg_per_product": flops,
+                      "tflops": flops / (ms * 1e-3) / 1e12, "kernels": kt,
                       "norm": float(y.norm().item())}), flush=True)
     s.close()
 
@@ -519,6 +681,10 @@ def main():
     ap.add_argument("--precision", default="tf32x3", choices=["fp64", "tf32", "bf16", "tf32x3"])
     ap.add_argument("--compare-fp64", dest="compare_fp64", action="store_true", default=True)
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
+    ap.add_argument("--arms", dest="arms", action="store_true", default=True,
+                    help="TF32 and BF16 arms and the g^2 scan {0.5, 2, 4} (one timed sweep each after three)")
+    ap.add_argument("--no-arms", dest="arms", action="store_false")
+    ap.add_argument("--no-probe", action="store_true", help="skip the in-run GEMM peak probes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--mode", default="sweep", choices=["sweep", "heff", "batch"],

@@ -438,6 +438,63 @@ def surface_layer(lat, s):
     return 1 + min(min(c[a], dims[a] - 1 - c[a]) for a in range(3))
 
 
+def bottom_heff_flops(state: TTN, idx):
+    """Algorithmic flops of one H_eff x at bottom node ``idx``: every term
+    with an environment factor (and the environment block Hamiltonian) is a
+    row selection of the node tensor by the monomial site operators
+    followed by a dense product with one environment block per output
+    charge sector, 2 * (nonzero rows) * chi_out * chi_in flops; terms that
+    act on the two sites only are row rescalings and count no flops.  A row
+    is nonzero when both site operators have an entry in it and its source
+    row lies in a charge block the parent bond carries."""
+    nd = state.nodes[idx]
+    assert all(kind == "site" for kind, _ in nd.children)
+    ql, qr, qc = state.labels[idx]
+    chi_q = {q: int(np.sum(qc == q)) for q in np.unique(qc)}
+    sites = [cid for _, cid in nd.children]
+    comp = state.all_sites - state.region[idx]
+    d = _basis.D_LOCAL
+
+    def row_source(op):
+        # source index of every row of a monomial operator (-1: zero row)
+        src = np.full(d, -1)
+        if op is None:
+            return np.arange(d)
+        op = op.tocsr()
+        for r in range(d):
+            lo, hi = op.indptr[r], op.indptr[r + 1]
+            if hi > lo:
+                src[r] = op.indices[lo]
+        return src
+
+    def count(srcA, srcB):
+        flops = 0.0
+        qs = ql[:, None] + qr[None, :]
+        ok = (srcA[:, None] >= 0) & (srcB[None, :] >= 0)
+        sa, sb = np.maximum(srcA, 0), np.maximum(srcB, 0)
+        qsrc = ql[sa][:, None] + qr[sb][None, :]
+        ok &= np.isin(qsrc, list(chi_q))
+        for q_out, c_out in chi_q.items():
+            sel = ok & (qs == q_out)
+            if not sel.any():
+                continue
+            for q_in in np.unique(qsrc[sel]):
+                flops += 2.0 * np.sum(sel & (qsrc == q_in)) * c_out * chi_q[int(q_in)]
+        return flops
+
+    total = 0.0
+    if nd.parent >= 0:
+        total += count(np.arange(d), np.arange(d))   # environment block Hamiltonian
+    for tm in state.terms:
+        on = {s for s, _ in tm.ops}
+        if not (on & comp) or not (on & set(sites)):
+            continue
+        A = state._site_factor(tm, sites[0])
+        B = state._site_factor(tm, sites[1])
+        total += count(row_source(A), row_source(B))
+    return total
+
+
 def expectation(state: TTN, p: _model.Params):
     """<psi|H(p)|psi> for the state's tensors under another coupling set p on
     the same lattice, by renormalizing every bond from scratch (centre moved

@@ -291,6 +291,21 @@ void TcPlan::release() {
   for (size_t& c : cap) c = 0;
 }
 
+void TgPlan::upload(cudaStream_t s) {
+  grow_upload(d_tiles, cap[0], tiles, s);
+  grow_upload(d_outs, cap[1], outs, s);
+  grow_upload(d_chunks, cap[2], chunks, s);
+  grow_upload(d_red, cap[3], red, s);
+}
+
+void TgPlan::release() {
+  void* ptrs[4] = {d_tiles, d_outs, d_chunks, d_red};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  d_tiles = nullptr; d_outs = nullptr; d_chunks = nullptr; d_red = nullptr;
+  for (size_t& c : cap) c = 0;
+}
+
 static KChunk make_chunk() {
   KChunk c;
   std::memset(&c, 0, sizeof(c));
@@ -661,6 +676,10 @@ Engine::~Engine() {
     cudaFree(kv.second.ld);
     cudaFree(kv.second.status);
   }
+  tg_cache_.clear();
+  if (tg_pool_) cudaFree(tg_pool_);
+  if (tg_scratch_) cudaFree(tg_scratch_);
+  if (ident_) cudaFree(ident_);
   if (xstage_) cudaFree(xstage_);
   if (xstage32_) cudaFree(xstage32_);
   if (wbuf_) cudaFree(wbuf_);
@@ -1754,6 +1773,14 @@ int Engine::apply_heff(const double* x, double* y, int cls) {
     if (y != y_out_) launch_copy(y_out_, y, n, stream_);
     return check(cudaGetLastError(), "apply_heff (mixed)") ? 0 : -3;
   }
+  if (use_mixed_ && cls < 0) {
+    // upper node in a mixed state: tensor-core leg contractions
+    if (x != x_in_) launch_copy(x, x_in_, n, stream_);
+    int rc = apply_heff_tg();
+    if (rc) return rc;
+    if (y != y_out_) launch_copy(y_out_, y, n, stream_);
+    return 0;
+  }
   HeffPlans* hp = heff_plans(center_, cls, false);
   if (!hp) return -1;
   if (x != x_in_) launch_copy(x, x_in_, n, stream_);
@@ -1763,9 +1790,8 @@ int Engine::apply_heff(const double* x, double* y, int cls) {
     // Z blocks that no source block maps to must read as zero
     cudaMemsetAsync(zpool_, 0, hp->z_elems * sizeof(double), stream_);
   }
-  const int fp32 = (use_mixed_ && cls < 0) ? 1 : 0;
   for (int i = 0; i < 3; ++i) {
-    const int rc = launch_kplan(hp->st[i], fp32, true);
+    const int rc = launch_kplan(hp->st[i], 0, true);
     if (rc) return rc;
   }
   if (profiling_) ev_end(e0, bottom ? KC_HEFF_SIMT_BOTTOM : KC_HEFF_SIMT_UPPER, hp->flops, hp->flops, 0.0);
@@ -2053,6 +2079,247 @@ int Engine::apply_heff_mixed() {
   }
   if (profiling_) ev_end(e0, KC_TC_HEFF, tc->flops_alg, tc->flops_exec, tc->bytes_alg);
   return 0;
+}
+
+// ------------------------------------------------------------------ tensor-core upper-node products
+namespace {
+constexpr int kTgRowsBig = 1 << 30;   // row split that keeps the row index linear
+
+// Cut an output into 128-row tiles; a long chunk list is split into parts
+// (partial sums added afterwards) when the plan has few tiles.
+void tg_tiles(TgPlan& pl, int oi, int parts_wanted) {
+  TgOut& o = pl.outs[oi];
+  const int cb = o.n_parts, ce = (int)pl.chunks.size();   // n_parts holds chunk_begin while building
+  long long steps = 0;
+  for (int c = cb; c < ce; ++c) steps += (pl.chunks[c].K + 31) / 32;
+  int parts = 1;
+  if (parts_wanted > 1 && steps >= 8) parts = (int)std::min<long long>(parts_wanted, steps / 4);
+  std::vector<std::pair<int, int>> ranges;
+  if (parts <= 1) {
+    ranges.push_back({cb, ce});
+  } else {
+    const long long per = (steps + parts - 1) / parts;
+    long long acc = 0;
+    int start = cb;
+    for (int c = cb; c < ce; ++c) {
+      acc += (pl.chunks[c].K + 31) / 32;
+      if (acc >= per && c + 1 < ce) { ranges.push_back({start, c + 1}); start = c + 1; acc = 0; }
+    }
+    ranges.push_back({start, ce});
+  }
+  o.n_parts = (int)ranges.size();
+  if (o.n_parts > 1) {
+    o.part_off = pl.scratch_need;
+    pl.scratch_need += (long long)o.n_parts * o.rows * o.N;
+    pl.red.push_back(oi);
+  }
+  for (int r0 = 0; r0 < o.rows; r0 += 128)
+    for (size_t p = 0; p < ranges.size(); ++p)
+      pl.tiles.push_back(TgTile{oi, r0, ranges[p].first, ranges[p].second, o.n_parts > 1 ? (int)p : -1});
+}
+}  // namespace
+
+// Plans of the mixed-precision upper-node product at `node`.  Every term's
+// operators on the two child legs are applied first (stage 0: the first one,
+// stage 1: the second one when a term has both), into FP32 intermediates that
+// keep the (a, b, c) element order of their blocks; stage 2 then forms every
+// output block of y as one K-concatenated sum over terms of the intermediate
+// (or x) times the term's parent-leg operator block, or times the identity
+// when the term has none there (the constant of Eq. (16) likewise).
+Engine::TgHeff* Engine::tg_plans(int node) {
+  auto it = tg_cache_.find(node);
+  if (it != tg_cache_.end()) return it->second.get();
+  std::vector<HTerm> hts;
+  build_heff_terms(node, -1, &hts);
+  const Layout& L = layout_[node];
+  std::map<int, Layout> lays;
+  long long zsize = 0;
+  for (int sh = -2; sh <= 2; ++sh) {
+    lays[sh] = shifted(node, sh);
+    zsize = std::max(zsize, lays[sh].size);
+  }
+  int nz = 0;
+  for (const HTerm& h : hts) nz += (h.op[0].kind ? 1 : 0) + (h.op[1].kind ? 1 : 0);
+  if ((long long)nz * zsize > tg_pool_elems_) {
+    cudaStreamSynchronize(stream_);   // cached plans point into the old pool
+    tg_cache_.clear();
+    if (tg_pool_) { untrack(tg_pool_); cudaFree(tg_pool_); tg_pool_ = nullptr; }
+    tg_pool_elems_ = (long long)std::max(nz, 1) * zsize + zsize;
+    device_alloc((void**)&tg_pool_, tg_pool_elems_ * sizeof(float), "tensor-core intermediates");
+    track(tg_pool_, tg_pool_elems_ * sizeof(float));
+  }
+  const int d0 = L.leg[0].total(), d1 = L.leg[1].total(), d2 = L.leg[2].total();
+  int dmax = 1;
+  for (const Sectors& b : bonds_) dmax = std::max(dmax, b.total());
+  dmax = std::max(dmax, std::max(d0, std::max(d1, d2)));
+  if (dmax > ident_dim_) {
+    cudaStreamSynchronize(stream_);   // cached plans point at the old identity
+    tg_cache_.clear();
+    if (ident_) { untrack(ident_); cudaFree(ident_); }
+    ident_dim_ = dmax;
+    device_alloc((void**)&ident_, (size_t)dmax * dmax * sizeof(double), "identity blocks");
+    track(ident_, (size_t)dmax * dmax * sizeof(double));
+    std::vector<double> h((size_t)dmax * dmax, 0.0);
+    for (int i = 0; i < dmax; ++i) h[(size_t)i * dmax + i] = 1.0;
+    cudaMemcpyAsync(ident_, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, stream_);
+    cudaStreamSynchronize(stream_);
+  }
+  std::unique_ptr<TgHeff> tp(new TgHeff);
+  TgHeff& T = *tp;
+  // Z = op (x)_leg X on the child legs, block by block; written[] marks the
+  // output blocks that receive a source block (the others are never read)
+  auto leg_apply = [&](TgPlan& pl, const Layout& LX, const void* X, bool x_f32, const std::vector<char>* xw,
+                       const Layout& LY, float* Y, std::vector<char>* yw, int leg, const OpRef& op, int shiftP,
+                       int dimP) {
+    const Sectors& S = LX.leg[leg];
+    for (size_t bi = 0; bi < LX.blk.size(); ++bi) {
+      if (xw && !(*xw)[bi]) continue;
+      const Layout::Blk& b = LX.blk[bi];
+      const int src = leg == 0 ? b.ia : b.ib;
+      const int dst = S.find(S.q[src] + shiftP);
+      if (dst < 0) continue;
+      const int k = LY.find(leg == 0 ? dst : b.ia, leg == 0 ? b.ib : dst);
+      if (k < 0 || LY.blk[k].ic != b.ic) continue;
+      const Layout::Blk& yb = LY.blk[k];
+      (*yw)[k] = 1;
+      TgOut o{};
+      o.C = Y + yb.off;
+      o.c_f32 = 1;
+      o.accumulate = 0;
+      TgChunk c{};
+      c.A = x_f32 ? (const void*)((const float*)X + b.off) : (const void*)((const double*)X + b.off);
+      c.a_f32 = x_f32 ? 1 : 0;
+      c.alpha = 1.0f;
+      const long long prow = S.offset(dst), pcol = S.offset(src);
+      c.B = op.ptr + prow * dimP + pcol;   // element (j = output index, k = input index)
+      c.bj = dimP;
+      c.bk = 1;
+      if (leg == 0) {
+        // rows (b, c) linear, K = a with stride db dc; out (a', b, c)
+        o.rows = b.db * b.dc; o.N = yb.da;
+        o.R2 = kTgRowsBig; o.t1 = 0; o.t2 = 1; o.cj = (long long)yb.db * yb.dc;
+        c.R2 = kTgRowsBig; c.s1 = 0; c.s2 = 1; c.sk = (long long)b.db * b.dc; c.K = b.da;
+      } else {
+        // rows (a, c), K = b with stride dc; out (a, b', c)
+        o.rows = b.da * b.dc; o.N = yb.db;
+        o.R2 = b.dc; o.t1 = (long long)yb.db * yb.dc; o.t2 = 1; o.cj = yb.dc;
+        c.R2 = b.dc; c.s1 = (long long)b.db * b.dc; c.s2 = 1; c.sk = b.dc; c.K = b.db;
+      }
+      o.npad = (o.N + 15) / 16 * 16;
+      pl.max_npad = std::max(pl.max_npad, o.npad);
+      o.n_parts = (int)pl.chunks.size();   // chunk_begin while building
+      pl.chunks.push_back(c);
+      pl.flops += 2.0 * o.rows * o.N * c.K;
+      pl.outs.push_back(o);
+      tg_tiles(pl, (int)pl.outs.size() - 1, 1);
+    }
+  };
+  struct Src { const void* Z; bool f32; int shift; std::vector<char> written; };
+  std::vector<Src> srcs;
+  float* zp = tg_pool_;
+  for (const HTerm& h : hts) {
+    Src sr{x_in_, false, 0, {}};
+    if (h.op[0].kind && h.op[1].kind) {
+      const int s0 = h.op[0].shift, s1 = h.op[1].shift;
+      std::vector<char> w1(lays[s0].blk.size(), 0), w2(lays[s0 + s1].blk.size(), 0);
+      leg_apply(T.st[0], L, x_in_, false, nullptr, lays[s0], zp, &w1, 0, h.op[0], s0, d0);
+      leg_apply(T.st[1], lays[s0], zp, true, &w1, lays[s0 + s1], zp + zsize, &w2, 1, h.op[1], s1, d1);
+      sr = Src{zp + zsize, true, s0 + s1, w2};
+      zp += 2 * zsize;
+    } else if (h.op[0].kind || h.op[1].kind) {
+      const int leg = h.op[0].kind ? 0 : 1;
+      const int sh = h.op[leg].shift;
+      std::vector<char> w(lays[sh].blk.size(), 0);
+      leg_apply(T.st[0], L, x_in_, false, nullptr, lays[sh], zp, &w, leg, h.op[leg], sh, leg == 0 ? d0 : d1);
+      sr = Src{zp, true, sh, w};
+      zp += zsize;
+    }
+    srcs.push_back(std::move(sr));
+  }
+  // stage 2: one output per block of y, chunks over terms
+  TgPlan& s3 = T.st[2];
+  const double cst = constant_;
+  int base_tiles = 0;
+  for (const Layout::Blk& yb : L.blk) base_tiles += (yb.da * yb.db + 127) / 128;
+  const int parts_wanted = std::max(1, std::min(16, (4 * 152) / std::max(1, base_tiles)));
+  for (const Layout::Blk& yb : L.blk) {
+    TgOut o{};
+    o.C = y_out_ + yb.off;
+    o.c_f32 = 0;
+    o.accumulate = 0;
+    o.rows = yb.da * yb.db;
+    o.N = yb.dc;
+    o.npad = (o.N + 15) / 16 * 16;
+    o.R2 = kTgRowsBig; o.t1 = 0; o.t2 = yb.dc; o.cj = 1;
+    s3.max_npad = std::max(s3.max_npad, o.npad);
+    o.n_parts = (int)s3.chunks.size();
+    auto add = [&](const void* Z, bool f32, long long zoff, int dcz, const double* B, long long bj, long long bk,
+                   double alpha, bool identity) {
+      TgChunk c{};
+      c.A = f32 ? (const void*)((const float*)Z + zoff) : (const void*)((const double*)Z + zoff);
+      c.a_f32 = f32 ? 1 : 0;
+      c.R2 = kTgRowsBig; c.s1 = 0; c.s2 = dcz; c.sk = 1; c.K = dcz;
+      c.B = B; c.bj = bj; c.bk = bk;
+      c.alpha = (float)alpha;
+      s3.chunks.push_back(c);
+      if (!identity) s3.flops += 2.0 * o.rows * o.N * dcz;
+    };
+    if (cst != 0.0) add(x_in_, false, yb.off, yb.dc, ident_, ident_dim_, 1, cst, true);
+    for (size_t t = 0; t < hts.size(); ++t) {
+      const HTerm& h = hts[t];
+      const Layout& LZ = lays[srcs[t].shift];
+      const int k = LZ.find(yb.ia, yb.ib);
+      if (k < 0) continue;
+      if (!srcs[t].written.empty() && !srcs[t].written[k]) continue;
+      const Layout::Blk& zb = LZ.blk[k];
+      if (h.op[2].kind == 1) {
+        if (L.leg[2].find(L.leg[2].q[zb.ic] + h.op[2].shift) != yb.ic) continue;
+        add(srcs[t].Z, srcs[t].f32, zb.off, zb.dc,
+            h.op[2].ptr + (long long)L.leg[2].offset(yb.ic) * d2 + L.leg[2].offset(zb.ic), d2, 1, h.coef, false);
+      } else {
+        if (zb.ic != yb.ic) continue;
+        add(srcs[t].Z, srcs[t].f32, zb.off, zb.dc, ident_, ident_dim_, 1, h.coef, true);
+      }
+    }
+    s3.outs.push_back(o);
+    tg_tiles(s3, (int)s3.outs.size() - 1, parts_wanted);
+  }
+  long long scratch = 0;
+  for (int i = 0; i < 3; ++i) {
+    T.st[i].upload(stream_);
+    scratch = std::max(scratch, T.st[i].scratch_need);
+    T.flops += T.st[i].flops;
+  }
+  if (scratch > tg_scratch_elems_) {
+    if (tg_scratch_) { untrack(tg_scratch_); cudaFree(tg_scratch_); }
+    tg_scratch_elems_ = scratch + scratch / 4;
+    device_alloc((void**)&tg_scratch_, tg_scratch_elems_ * sizeof(float), "tensor-core partial sums");
+    track(tg_scratch_, tg_scratch_elems_ * sizeof(float));
+  }
+  if (!check(cudaGetLastError(), "tensor-core plan")) return nullptr;
+  TgHeff* raw = tp.get();
+  tg_cache_[node] = std::move(tp);
+  return raw;
+}
+
+int Engine::apply_heff_tg() {
+  TgHeff* T = tg_plans(center_);
+  if (!T) return -1;
+  const int elem = precision_ == PREC_BF16 ? 2 : 4;
+  const int split = precision_ == PREC_TF32X3 ? 1 : 0;
+  cudaEvent_t e0 = nullptr;
+  if (profiling_) ev_begin(&e0);
+  for (int i = 0; i < 3; ++i) {
+    TgPlan& pl = T->st[i];
+    const int rc = launch_tg_gemm(elem, split, pl.d_tiles, (int)pl.tiles.size(), pl.d_outs, pl.d_chunks, pl.max_npad,
+                                  tg_scratch_, pl.d_red, (int)pl.red.size(), d_err_, stream_, wait_polls);
+    if (rc) {
+      err_ = "tensor-core contraction: output width outside the supported range";
+      return rc;
+    }
+  }
+  if (profiling_) ev_end(e0, KC_HEFF_SIMT_UPPER, T->flops, T->flops, 0.0);
+  return check(cudaGetLastError(), "tensor-core contraction") ? 0 : -3;
 }
 
 // ------------------------------------------------------------------ profiling

@@ -167,6 +167,25 @@ struct TcPlan {
   ~TcPlan() { release(); }
 };
 
+// Tensor-core leg-contraction plan (one launch of launch_tg_gemm).
+struct TgPlan {
+  std::vector<TgTile> tiles;
+  std::vector<TgOut> outs;
+  std::vector<TgChunk> chunks;
+  std::vector<int> red;
+  TgTile* d_tiles = nullptr;
+  TgOut* d_outs = nullptr;
+  TgChunk* d_chunks = nullptr;
+  int* d_red = nullptr;
+  size_t cap[4] = {0, 0, 0, 0};
+  long long scratch_need = 0;   // floats of split-K partial sums
+  int max_npad = 16;
+  double flops = 0.0;           // algorithmic: 2 rows N K over the non-identity chunks
+  void upload(cudaStream_t s);
+  void release();
+  ~TgPlan() { release(); }
+};
+
 // Per kernel-class timing of launches on the engine stream (CUDA events).
 // SIMT classes run FP64, or FP32 inside the low-precision phase of a mixed state.
 // KC_MOVE and KC_LANCZOS time whole phases (centre moves with QR and
@@ -339,6 +358,22 @@ class Engine {
   // mixed-precision state: per-node plans; the staging buffers are shared
   // and the environment blocks are re-staged when the centre changes
   std::map<int, std::unique_ptr<TcPlan>> tc_cache_;
+  // mixed-precision upper-node products on the tensor cores: three stages
+  // per node (first child leg, second child leg, parent leg with the sum over
+  // terms); FP32 intermediates in tg_pool_, identity blocks in ident_
+  struct TgHeff {
+    TgPlan st[3];
+    double flops = 0.0;
+  };
+  std::map<int, std::unique_ptr<TgHeff>> tg_cache_;
+  float* tg_pool_ = nullptr;
+  long long tg_pool_elems_ = 0;
+  float* tg_scratch_ = nullptr;
+  long long tg_scratch_elems_ = 0;
+  double* ident_ = nullptr;
+  int ident_dim_ = 0;
+  TgHeff* tg_plans(int node);
+  int apply_heff_tg();
   int tc_w_node_ = -1;          // node whose environment blocks are staged
   void clear_tc_cache();
   void* xstage_ = nullptr;      // BF16 or FP32 padded staging of x

@@ -182,6 +182,51 @@ struct ConvJob {
 int launch_tc_heff(int elem, int split, const TcTile* tiles, int n_tiles, const TcOutput* outs,
                    const TcChunk* chunks, const TcAdd* adds, int max_kpad, int max_npad, int* err, cudaStream_t s,
                    long long polls = -1);
+// ---- grouped leg contractions on the tensor cores (tcgen05) ----
+// One contribution D[r, j] += alpha * sum_{k < K} A(r, k) B(j, k):
+//   A(r, k) = A[(r / R2) * s1 + (r % R2) * s2 + k * sk]  (float if a_f32, else double)
+//   B(j, k) = B[j * bj + k * bk]                          (double)
+struct TgChunk {
+  const void* A;
+  long long s1, s2, sk;
+  const double* B;
+  long long bj, bk;
+  int R2;
+  int K;
+  int a_f32;
+  float alpha;
+};
+// An output: D[r, j] (r < rows, j < N) at C[(r / R2) * t1 + (r % R2) * t2 + j * cj],
+// float if c_f32 (else double), written or added (accumulate); chunks of its
+// tiles are summed in one accumulator; n_parts > 1: tiles write FP32 partial
+// sums (rows x N each, at scratch + part_off) that the reduction adds up.
+struct TgOut {
+  void* C;
+  long long t1, t2, cj;
+  int R2;
+  int rows, N, npad;
+  int c_f32;
+  int accumulate;
+  int n_parts;
+  long long part_off;
+};
+// One CTA: rows row0 .. row0 + 127 of output `out` over chunks [chunk_begin,
+// chunk_end); part >= 0 writes partial slot `part`.
+struct TgTile {
+  int out;
+  int row0;
+  int chunk_begin, chunk_end;
+  int part;
+};
+// Shared memory of one launch (two stages of A and B tiles).
+int tg_stage_bytes(int elem, int split, int max_npad, int* a_bytes, int* b_bytes);
+// elem 4: TF32 operands (split: three products of hi / lo parts), 2: BF16.
+// red_list: outputs with n_parts > 1 (reduced after the GEMM).  err: device
+// flag set if a wait timed out; polls < 0: default bound.
+int launch_tg_gemm(int elem, int split, const TgTile* tiles, int n_tiles, const TgOut* outs, const TgChunk* chunks,
+                   int max_npad, float* scratch, const int* red_list, int n_red, int* err, cudaStream_t s,
+                   long long polls = -1);
+
 // mode 0: plain (BF16 or FP32 by elem); mode 1: split x rows [hi | lo] of
 // width 2 kpad; mode 2: split W rows [hi | lo] of width 2 kpad.  hi is
 // the value with its 13 low mantissa bits cleared (what the TF32 units read).

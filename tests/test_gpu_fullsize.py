@@ -131,3 +131,23 @@ def test_mixed_update_full_size(q, prec):
         assert abs(em - e64) < 1e-6 * abs(e64), (prec, node, em, e64)
         s.node_import(node, t0)
     s.close()
+
+
+@pytest.mark.parametrize("L,chi,seed", [((2, 2, 2), 8, 0), ((4, 4, 4), 64, 1)])
+def test_bottom_flop_count_matches_oracle(q, L, chi, seed):
+    """The algorithmic flops the library books for one tensor-core product
+    at bottom node 0 equal the oracle's own count of the same product (a
+    row selection per term, then one dense environment block per charge
+    sector: 2 x nonzero rows x chi_out x chi_in)."""
+    c = workloads.qed_couplings(1.0)
+    ref = ottn.TTN(omodel.Params(*L, Q=0, **c), chi, seed, build_ops=False)
+    want = ottn.bottom_heff_flops(ref, 0)
+    s = q.TTN(q.Model(*L, Q=0, **c), chi, seed=seed, precision="tf32x3")
+    s.move_center(0)
+    s.set_profiling(True)
+    s.reset_timing()
+    s.apply_heff(np.ones(s.node_size(0)))
+    t = s.kernel_timing("tc_heff")
+    s.close()
+    got = t["flops_alg"] / max(1, t["launches"])
+    assert abs(got - want) <= 1e-9 * want, (got, want)
