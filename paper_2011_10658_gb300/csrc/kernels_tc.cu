@@ -281,15 +281,27 @@ int launch_tc_heff(int elem, int split, const TcTile* tiles, int n_tiles, const 
   if (smem > 200 * 1024 || max_npad > 256 || max_npad % 16 || max_kpad % 16) return -7;
   if (split && elem != 4) return -7;
   if (elem == 2) {
-    cudaFuncSetAttribute(tc_heff_kernel<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    static bool attr_2f = false;   // set once: host attribute calls cost as much as a launch
+    if (!attr_2f) {
+      cudaFuncSetAttribute(tc_heff_kernel<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr_2f = true;
+    }
     tc_heff_kernel<2, false><<<n_tiles, TC_THREADS, smem, s>>>(tiles, outs, chunks, adds, a_bytes, b_bytes, err, polls);
     count_launches(1);
   } else if (!split) {
-    cudaFuncSetAttribute(tc_heff_kernel<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    static bool attr_4f = false;   // set once: host attribute calls cost as much as a launch
+    if (!attr_4f) {
+      cudaFuncSetAttribute(tc_heff_kernel<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr_4f = true;
+    }
     tc_heff_kernel<4, false><<<n_tiles, TC_THREADS, smem, s>>>(tiles, outs, chunks, adds, a_bytes, b_bytes, err, polls);
     count_launches(1);
   } else {
-    cudaFuncSetAttribute(tc_heff_kernel<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    static bool attr_4t = false;   // set once: host attribute calls cost as much as a launch
+    if (!attr_4t) {
+      cudaFuncSetAttribute(tc_heff_kernel<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr_4t = true;
+    }
     tc_heff_kernel<4, true><<<n_tiles, TC_THREADS, smem, s>>>(tiles, outs, chunks, adds, a_bytes, b_bytes, err, polls);
     count_launches(1);
   }

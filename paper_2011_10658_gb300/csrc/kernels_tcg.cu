@@ -26,6 +26,9 @@
 // Every mbarrier wait is bounded (polls, a launch argument); a timeout sets
 // *err, and the CTA then drains its MMAs through a commit to a fresh barrier
 // (waited on with the default bound), frees its TMEM and returns.
+#include <algorithm>
+#include <map>
+
 #include <cuda_bf16.h>
 
 #include "kernels.cuh"
@@ -35,7 +38,7 @@ namespace qed {
 namespace {
 
 constexpr int TG_THREADS = 128;
-constexpr int TG_KB = 32;                         // K elements per stage
+constexpr int TG_KB = 16;                         // K elements per stage
 constexpr long long kTgWaitPolls = 1LL << 22;
 
 __device__ __forceinline__ uint32_t tg_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -131,22 +134,18 @@ __device__ __forceinline__ void tg_put4(uint8_t* base, int row, int q4, const fl
 }
 
 template <int ELEM, bool SPLIT>
-__global__ void __launch_bounds__(TG_THREADS) tg_gemm_kernel(const TgTile* __restrict__ tiles,
+__global__ void __launch_bounds__(TG_THREADS) tg_gemm_kernel(const TgTile* __restrict__ tiles, int n_tiles,
                                                               const TgOut* __restrict__ outs,
                                                               const TgChunk* __restrict__ chunks,
                                                               float* __restrict__ scratch, int a_bytes, int b_bytes,
-                                                              int* err, long long polls) {
+                                                              int max_npad, int* err, long long polls) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ uint32_t tmem_slot;
   __shared__ __align__(8) uint64_t mbar[3];   // two stages, one drain
   __shared__ int s_fail;
-  const TgTile tile = tiles[blockIdx.x];
-  const TgOut out = outs[tile.out];
   const int tid = threadIdx.x, warp = tid >> 5;
-  uint8_t* Abuf[2] = {smem, smem + a_bytes};
-  uint8_t* Bbuf[2] = {smem + 2 * a_bytes, smem + 2 * a_bytes + b_bytes};
   uint32_t ncols = 32;
-  while ((int)ncols < out.npad) ncols <<= 1;
+  while ((int)ncols < max_npad) ncols <<= 1;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tg_smem_u32(&tmem_slot)),
                  "r"(ncols));
@@ -161,20 +160,26 @@ __global__ void __launch_bounds__(TG_THREADS) tg_gemm_kernel(const TgTile* __res
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
-  const int row = tile.row0 + tid;
-  const bool row_ok = row < out.rows;
-  // D = F32; A, B = TF32 (kind::tf32) or BF16 (kind::f16), both K-major; M = 128
-  uint32_t idesc = (1u << 4) | ((uint32_t)(out.npad >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-  idesc |= ELEM == 4 ? ((2u << 7) | (2u << 10)) : ((1u << 7) | (1u << 10));
+  // commits so far on the two stage barriers and on the drain barrier
+  uint32_t uses0 = 0u, uses1 = 0u, drains = 0u;
+  uint8_t* const A0 = smem;
+  uint8_t* const A1 = smem + a_bytes;
+  uint8_t* const B0 = smem + 2 * a_bytes;
+  uint8_t* const B1 = smem + 2 * a_bytes + b_bytes;
 
-  // steps = (chunk, k0) pairs of this tile, in order
-  int ci = tile.chunk_begin, k0 = 0;
-  auto load_step = [&](int c_idx, int kk0, int b) {
+  // stage `st` is about to be overwritten: wait for the MMAs that last read it
+  auto free_stage = [&](int st) {
+    const uint32_t u = st ? uses1 : uses0;
+    if (u > 0 && !tg_wait(tg_smem_u32(&mbar[st]), (u - 1) & 1, polls)) s_fail = 1;
+  };
+  // K values k0 .. k0 + TG_KB of chunk ci of `tile` into stage buffers Ab, Bb
+  auto load_step = [&](const TgTile& tile, const TgOut& out, int c_idx, int kk0, uint8_t* Ab, uint8_t* Bb) {
     const TgChunk c = chunks[c_idx];
-    // A: this thread's row r, K values kk0 .. kk0 + TG_KB
+    const int row = tile.row0 + tid;
+    const bool row_ok = row < out.rows;
     long long base = 0;
     if (row_ok) base = (long long)(row / c.R2) * c.s1 + (long long)(row % c.R2) * c.s2;
-#pragma unroll 2
+#pragma unroll
     for (int q4 = 0; q4 < TG_KB / 4; ++q4) {
       float v[4];
 #pragma unroll
@@ -187,9 +192,8 @@ __global__ void __launch_bounds__(TG_THREADS) tg_gemm_kernel(const TgTile* __res
         }
         v[i] = x;
       }
-      tg_put4<ELEM, SPLIT>(Abuf[b], tid, q4, v);
+      tg_put4<ELEM, SPLIT>(Ab, tid, q4, v);
     }
-    // B: out.npad rows j, scaled by alpha
     const float alpha = c.alpha;
     for (int e = tid; e < out.npad * (TG_KB / 4); e += TG_THREADS) {
       const int j = e / (TG_KB / 4), q4 = e % (TG_KB / 4);
@@ -199,103 +203,157 @@ __global__ void __launch_bounds__(TG_THREADS) tg_gemm_kernel(const TgTile* __res
         const int k = kk0 + 4 * q4 + i;
         v[i] = (j < out.N && k < c.K) ? alpha * tg_d2f(__ldg(c.B + (long long)j * c.bj + (long long)k * c.bk)) : 0.f;
       }
-      tg_put4<ELEM, SPLIT>(Bbuf[b], j, q4, v);
+      tg_put4<ELEM, SPLIT>(Bb, j, q4, v);
     }
   };
-  auto advance = [&]() {
-    k0 += TG_KB;
-    if (k0 >= chunks[ci].K) { ++ci; k0 = 0; }
+  // rows of `tile` from TMEM (or zeros) to the output or its partial slot
+  auto store_tile = [&](const TgTile& tile, const TgOut& out, bool from_tmem, bool ok) {
+    const int row = tile.row0 + tid;
+    const bool row_ok = row < out.rows;
+    long long cbase = 0;
+    if (row_ok) cbase = (long long)(row / out.R2) * out.t1 + (long long)(row % out.R2) * out.t2;
+    for (int c0 = 0; c0 < out.N; c0 += 16) {
+      uint32_t v[16];
+      if (from_tmem) {
+        const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = 0u;
+      }
+      if (!row_ok) continue;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int col = c0 + j;
+        if (col >= out.N) break;
+        const float f = ok ? __uint_as_float(v[j]) : 0.f;
+        if (tile.part >= 0) {
+          scratch[out.part_off + (long long)tile.part * out.rows * out.N + (long long)row * out.N + col] = f;
+        } else if (out.c_f32) {
+          float* p = (float*)out.C + cbase + (long long)col * out.cj;
+          *p = out.accumulate ? *p + f : f;
+        } else {
+          double* p = (double*)out.C + cbase + (long long)col * out.cj;
+          *p = out.accumulate ? *p + (double)f : (double)f;
+        }
+      }
+    }
+  };
+  // next tile of this CTA that has chunks; tiles without any get zeros
+  auto next_tile = [&](int from) {
+    int t = from;
+    while (t < n_tiles) {
+      const TgTile tl = tiles[t];
+      if (tl.chunk_end > tl.chunk_begin) break;
+      store_tile(tl, outs[tl.out], false, true);
+      t += gridDim.x;
+    }
+    return t;
   };
 
-  uint32_t uses[2] = {0u, 0u};
-  int step = 0;
-  const bool any = tile.chunk_end > tile.chunk_begin;
-  if (any) {
-    load_step(ci, k0, 0);
+  // The CTA walks the steps (chunk, K slab) of its tiles blockIdx.x,
+  // blockIdx.x + gridDim.x, ... as one sequence on two shared-memory stages:
+  // the next step's operands are loaded while the current step's MMAs run,
+  // across tile boundaries too (the next tile's first step is loaded before
+  // the current tile's accumulator is drained and stored).
+  int ti = next_tile(blockIdx.x);
+  if (ti < n_tiles) {
+    TgTile tile = tiles[ti];
+    TgOut out = outs[tile.out];
+    int ci = tile.chunk_begin, k0 = 0, b = 0;
+    bool first = true;
+    load_step(tile, out, ci, k0, A0, B0);
     asm volatile("fence.proxy.async.shared::cta;");
     __syncthreads();
     while (true) {
-      const int b = step & 1;
       if (tid == 0) {
+        // D = F32; A, B = TF32 (kind::tf32) or BF16 (kind::f16), K-major; M = 128
+        uint32_t idesc = (1u << 4) | ((uint32_t)(out.npad >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+        idesc |= ELEM == 4 ? ((2u << 7) | (2u << 10)) : ((1u << 7) | (1u << 10));
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t a0 = tg_smem_u32(Abuf[b]), b0 = tg_smem_u32(Bbuf[b]);
+        const uint32_t a0 = tg_smem_u32(b ? A1 : A0), b0 = tg_smem_u32(b ? B1 : B0);
         if (!SPLIT) {
-          const int kch = TG_KB * ELEM / 16;
-          const uint32_t sbo = (uint32_t)kch * 128u;
+          constexpr int kch = TG_KB * ELEM / 16;
+          constexpr uint32_t sbo = (uint32_t)kch * 128u;
+#pragma unroll
           for (int ks = 0; ks < kch / 2; ++ks)
             tg_mma<ELEM>(tmem, tg_desc(a0 + ks * 256, 128, sbo), tg_desc(b0 + ks * 256, 128, sbo), idesc,
-                         (step > 0 || ks > 0) ? 1u : 0u);
+                         (!first || ks > 0) ? 1u : 0u);
         } else {
-          const int part = TG_KB / 4;   // 16-byte chunks of one of hi / lo
-          const uint32_t sbo = (uint32_t)(2 * part) * 128u;
-          const int pa[3] = {0, 0, part}, pb[3] = {0, part, 0};
+          constexpr int part = TG_KB / 4;   // 16-byte chunks of one of hi / lo
+          constexpr uint32_t sbo = (uint32_t)(2 * part) * 128u;
+#pragma unroll
           for (int g = 0; g < 3; ++g)
-            for (int ks = 0; ks < part / 2; ++ks)
-              tg_mma<ELEM>(tmem, tg_desc(a0 + (pa[g] + 2 * ks) * 128, 128, sbo),
-                           tg_desc(b0 + (pb[g] + 2 * ks) * 128, 128, sbo), idesc,
-                           (step > 0 || g > 0 || ks > 0) ? 1u : 0u);
+#pragma unroll
+            for (int ks = 0; ks < part / 2; ++ks) {
+              const int pa = g == 2 ? part : 0, pb = g == 1 ? part : 0;
+              tg_mma<ELEM>(tmem, tg_desc(a0 + (pa + 2 * ks) * 128, 128, sbo),
+                           tg_desc(b0 + (pb + 2 * ks) * 128, 128, sbo), idesc,
+                           (!first || g > 0 || ks > 0) ? 1u : 0u);
+            }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
             tg_smem_u32(&mbar[b])));
       }
-      uses[b] += 1;
-      advance();
-      if (ci >= tile.chunk_end) break;
-      const int nb = b ^ 1;
-      if (uses[nb] > 0 && !tg_wait(tg_smem_u32(&mbar[nb]), (uses[nb] - 1) & 1, polls)) s_fail = 1;
-      load_step(ci, k0, nb);
+      if (b) ++uses1; else ++uses0;
+      first = false;
+      // the step after this one
+      int nci = ci, nk0 = k0 + TG_KB, nti = ti;
+      if (nk0 >= chunks[ci].K) { ++nci; nk0 = 0; }
+      const bool tile_done = nci >= tile.chunk_end;
+      TgTile ntile = tile;
+      TgOut nout = out;
+      if (tile_done) {
+        nti = next_tile(ti + gridDim.x);
+        if (nti < n_tiles) {
+          ntile = tiles[nti];
+          nout = outs[ntile.out];
+          nci = ntile.chunk_begin;
+          nk0 = 0;
+        }
+      }
+      const bool more = nti < n_tiles;
+      if (more) {
+        free_stage(b ^ 1);
+        load_step(ntile, nout, nci, nk0, b ? A0 : A1, b ? B0 : B1);
+      }
+      if (tile_done) {
+        // drain every MMA of this tile, then its accumulator to global memory
+        if (tid == 0)
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              tg_smem_u32(&mbar[2])));
+        if (!tg_wait(tg_smem_u32(&mbar[2]), drains & 1u, polls)) {
+          s_fail = 1;
+          tg_wait(tg_smem_u32(&mbar[2]), drains & 1u, kTgWaitPolls);
+        }
+        ++drains;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        store_tile(tile, out, true, s_fail == 0);
+        first = true;
+      }
+      if (!more) break;
+      // the next step's operands are visible to the tensor cores, and every
+      // TMEM read of a finished tile precedes the next tile's MMAs
+      asm volatile("tcgen05.fence::before_thread_sync;");
       asm volatile("fence.proxy.async.shared::cta;");
       __syncthreads();
-      ++step;
-    }
-    // drain every MMA this CTA issued before TMEM is read or freed
-    if (tid == 0)
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          tg_smem_u32(&mbar[2])));
-    if (!tg_wait(tg_smem_u32(&mbar[2]), 0, polls)) {
-      s_fail = 1;
-      tg_wait(tg_smem_u32(&mbar[2]), 0, kTgWaitPolls);
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;");
-  }
-  __syncthreads();
-  const bool ok = s_fail == 0;
-  if (!ok && tid == 0) atomicExch(err, 1);
-  // epilogue: TMEM lanes 32*warp .. +31 hold rows row0 + 32*warp + lane
-  long long cbase = 0;
-  if (row_ok) cbase = (long long)(row / out.R2) * out.t1 + (long long)(row % out.R2) * out.t2;
-  for (int c0 = 0; c0 < out.N; c0 += 16) {
-    uint32_t v[16];
-    if (any) {
-      const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
-    } else {
-#pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = 0u;
-    }
-    if (!row_ok) continue;
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const int col = c0 + j;
-      if (col >= out.N) break;
-      const float f = ok ? __uint_as_float(v[j]) : 0.f;
-      if (tile.part >= 0) {
-        scratch[out.part_off + (long long)tile.part * out.rows * out.N + (long long)row * out.N + col] = f;
-      } else if (out.c_f32) {
-        float* p = (float*)out.C + cbase + (long long)col * out.cj;
-        *p = out.accumulate ? *p + f : f;
-      } else {
-        double* p = (double*)out.C + cbase + (long long)col * out.cj;
-        *p = out.accumulate ? *p + (double)f : (double)f;
-      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      tile = ntile;
+      out = nout;
+      ti = nti;
+      ci = nci;
+      k0 = nk0;
+      b ^= 1;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (s_fail && tid == 0) atomicExch(err, 1);
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
 }
@@ -338,19 +396,29 @@ int launch_tg_gemm(int elem, int split, const TgTile* tiles, int n_tiles, const 
   int a_bytes = 0, b_bytes = 0;
   const int smem = tg_stage_bytes(elem, split, max_npad, &a_bytes, &b_bytes);
   if (smem > 200 * 1024) return -7;
-  if (elem == 2) {
-    cudaFuncSetAttribute(tg_gemm_kernel<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    tg_gemm_kernel<2, false><<<n_tiles, TG_THREADS, smem, s>>>(tiles, outs, chunks, scratch, a_bytes, b_bytes, err,
-                                                               polls);
-  } else if (!split) {
-    cudaFuncSetAttribute(tg_gemm_kernel<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    tg_gemm_kernel<4, false><<<n_tiles, TG_THREADS, smem, s>>>(tiles, outs, chunks, scratch, a_bytes, b_bytes, err,
-                                                               polls);
-  } else {
-    cudaFuncSetAttribute(tg_gemm_kernel<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    tg_gemm_kernel<4, true><<<n_tiles, TG_THREADS, smem, s>>>(tiles, outs, chunks, scratch, a_bytes, b_bytes, err,
-                                                              polls);
+  // kernel attributes and occupancy are looked up once per configuration
+  // (host API calls of this kind cost as much as a small launch)
+  const int kind = elem == 2 ? 0 : (split ? 2 : 1);
+  auto kern = kind == 0 ? tg_gemm_kernel<2, false> : (kind == 2 ? tg_gemm_kernel<4, true> : tg_gemm_kernel<4, false>);
+  static bool attr_set[3] = {false, false, false};
+  static int sms = 0;
+  if (!attr_set[kind]) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set[kind] = true;
   }
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  int ncols = 32;
+  while (ncols < max_npad) ncols <<= 1;
+  // CTAs per SM from the resources one CTA holds: dynamic + static shared
+  // memory (227 KB per SM), TMEM columns (512 per SM), at most 8
+  const int per_sm = std::max(1, std::min(8, std::min(512 / ncols, (227 * 1024) / (smem + 2048))));
+  const int grid = std::min(n_tiles, sms * per_sm);
+  kern<<<grid, TG_THREADS, smem, s>>>(tiles, n_tiles, outs, chunks, scratch, a_bytes, b_bytes, max_npad, err, polls);
   count_launches(1);
   if (n_red > 0) {
     tg_reduce_kernel<<<dim3(16, n_red), 256, 0, s>>>(outs, red_list, scratch);
