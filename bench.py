@@ -50,7 +50,8 @@ Q = 0
 TOL = 1e-6
 KRYLOV = 64
 PRODUCT_CLASSES = ("tc_heff", "heff_simt_bottom", "heff_simt_upper")
-ALL_CLASSES = ("tc_heff", "heff_simt_bottom", "heff_simt_upper", "move", "lanczos", "move_qr", "move_ops")
+ALL_CLASSES = ("tc_heff", "heff_simt_bottom", "heff_simt_upper", "move", "lanczos", "move_qr", "move_ops",
+               "move_ops_bottom")
 
 
 def workload_name(prec, g2=G2):
@@ -305,8 +306,9 @@ def class_table(kt, elapsed_ms, peaks, precision):
     own = {"tc_heff": ("bf16" if precision == "bf16" else "tf32"),
            "heff_simt_bottom": "fp64",
            "heff_simt_upper": ("fp64" if precision == "fp64" else "fp32_simt"),
-           "move_ops": "fp64"}
-    for k in ("tc_heff", "heff_simt_bottom", "heff_simt_upper", "move_ops", "move_qr"):
+           "move_ops": "fp64",
+           "move_ops_bottom": ("fp64" if precision == "fp64" else "bf16")}
+    for k in ("tc_heff", "heff_simt_bottom", "heff_simt_upper", "move_ops", "move_ops_bottom", "move_qr"):
         v = kt[k]
         r = {"ms": v["ms"], "launches": v["launches"], "share_of_step": v["ms"] / elapsed_ms}
         if v["flops_alg"] > 0 and v["ms"] > 0:
@@ -397,7 +399,8 @@ def run_native(args):
 
     # roofline of the class with the most kernel time among the flop-counted
     # contraction classes (products and operator updates)
-    dom = max(("tc_heff", "heff_simt_bottom", "heff_simt_upper", "move_ops"), key=lambda k: kt[k]["ms"])
+    dom = max(("tc_heff", "heff_simt_bottom", "heff_simt_upper", "move_ops", "move_ops_bottom"),
+              key=lambda k: kt[k]["ms"])
     d = kt[dom]
     per_launch_ms = d["ms"] / max(1, d["launches"])
     achieved = d["flops_alg"] / max(1, d["launches"]) / (per_launch_ms * 1e-3) / 1e12

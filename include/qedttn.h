@@ -189,12 +189,15 @@ int ttn_last_update(ttn_state *s, int32_t *iters_fp64, int32_t *iters_mixed, dou
 
 /* Kernel timing with CUDA events on the state's stream (off by default).
  * kernel_class: 0 = tensor-core bottom-node H_eff, 1 = SIMT bottom-node
- * H_eff (FP64), 2 = SIMT upper-node H_eff (FP64, or FP32 in the
- * low-precision phase of a mixed state), 3 = whole centre moves (QR,
- * R absorption, operator updates), 4 = whole Lanczos calls (products
- * included; the difference is vector work and idle time), 5 = per-bond QR
- * and R absorption of a move, 6 = per-bond operator update of a move
- * (FP64; flops = its grouped-GEMM chunks).  Returns accumulated milliseconds,
+ * H_eff (FP64), 2 = upper-node H_eff (FP64 SIMT, or tensor-core leg
+ * contractions in the low-precision phase of a mixed state), 3 = whole
+ * centre moves (QR, R absorption, operator updates), 4 = whole Lanczos calls
+ * (products included; the difference is vector work and idle time), 5 =
+ * per-bond QR and R absorption of a move, 6 = per-bond operator update at an
+ * upper node (FP64; flops = its grouped-GEMM chunks), 7 = per-bond operator
+ * update leaving a bottom node upwards (FP64, or FP64-accurate digit-plane
+ * products on the tensor cores in a mixed state; flops = 2 x mapped rows x
+ * chi_out x chi_in per term and sector).  Returns accumulated milliseconds,
  * launches, algorithmic flops (nonzero rows of the monomial gathers times
  * the dense environment contraction), executed flops (padded tiles) and
  * algorithmic bytes (staged input read, FP64 output written, operator

@@ -180,8 +180,9 @@ class TTN:
     def kernel_timing(self, kernel_class):
         ms, n, fa, fe, ba = (ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_double(),
                              ctypes.c_double())
-        k = {"tc_heff": 0, "heff_simt_bottom": 1, "heff_simt_upper": 2, "move": 3,
-             "lanczos": 4, "move_qr": 5, "move_ops": 6}.get(kernel_class, kernel_class)
+        k = {"tc_heff": 0, "heff_simt_bottom": 1, "heff_simt_upper": 2, "heff_upper": 2, "move": 3,
+             "lanczos": 4, "move_qr": 5, "move_ops": 6, "move_ops_upper": 6,
+             "move_ops_bottom": 7}.get(kernel_class, kernel_class)
         check(lib().ttn_kernel_timing(self._h, k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(fa),
                                       ctypes.byref(fe), ctypes.byref(ba)))
         return dict(ms=ms.value, launches=n.value, flops_alg=fa.value, flops_exec=fe.value, bytes_alg=ba.value)

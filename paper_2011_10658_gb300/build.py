@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(os.path.dirname(HERE), "_build")
 LIB = os.path.join(HERE, "libqedttn.so")
 
-SOURCES = ["model.cpp", "kernels_fp64.cu", "kernels_tc.cu", "kernels_tcg.cu", "engine.cu", "batch.cu", "capi.cu",
+SOURCES = ["model.cpp", "kernels_fp64.cu", "kernels_tc.cu", "kernels_tcg.cu", "kernels_oz.cu", "engine.cu", "batch.cu", "capi.cu",
            "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]

@@ -3,7 +3,8 @@
 // moves per problem, then one lockstep Lanczos whose H_eff products for
 // all problems are a single grouped launch (tensor-core tiles of every
 // problem's bottom-node plan, or every problem's grouped-GEMM chunks above),
-// replayed from a CUDA graph once its tile shapes are tuned.  The vector
+// replayed from a CUDA graph once its tile shapes are tuned (upper nodes of a
+// mixed batch: every problem's tensor-core stage plans).  The vector
 // work of each problem follows on the same stream, and one wait per lockstep
 // iteration reads every problem's convergence data.  The FP64 check of a
 // mixed-precision update runs per problem afterwards.  Every problem does
@@ -29,14 +30,19 @@ struct BatchRunner::Grouped {
   std::vector<uint64_t> gens;   // members' plan-cache generations at build time
   double* scratch = nullptr;    // launcher's split-K scratch at capture time
   bool tc = false;
+  bool tg = false;              // upper node of a mixed batch: tensor-core leg contractions
+  bool launched = false;        // one eager launch before any graph capture
   int fp32 = 0;
   TcPlan tcp;
   KPlan st[3];
+  TgPlan tgs[3];
+  float* tg_scratch = nullptr;
   std::vector<std::pair<double*, long long>> zero;   // Z pools to clear before the stages
   cudaGraphExec_t exec = nullptr;
   long long graph_kernels = 0;
   ~Grouped() {
     if (exec) cudaGraphExecDestroy(exec);
+    if (tg_scratch) cudaFree(tg_scratch);
   }
 };
 
@@ -112,6 +118,40 @@ int BatchRunner::build(int node, const std::vector<int>& members, std::unique_pt
     upload_vec(b.d_chunks, b.cap[2], b.chunks, s);
     upload_vec(b.d_adds, b.cap[3], b.adds, s);
     upload_vec(b.d_xjobs, b.cap[4], b.xjobs, s);
+  } else if (mixed) {
+    // upper node, mixed: every member's tensor-core stage plans, concatenated
+    // stage by stage; partial sums rebased into one batch scratch
+    g->tg = true;
+    for (int m : members)
+      if (!es_[m]->tg_plans(node)) return -1;
+    long long scratch = 0;
+    for (int i = 0; i < 3; ++i) {
+      TgPlan& b = g->tgs[i];
+      long long part_base = 0;
+      for (int m : members) {
+        const TgPlan& p = es_[m]->tg_plans(node)->st[i];
+        const int o0 = (int)b.outs.size(), c0 = (int)b.chunks.size();
+        for (TgTile t : p.tiles) {
+          t.out += o0;
+          t.chunk_begin += c0;
+          t.chunk_end += c0;
+          b.tiles.push_back(t);
+        }
+        for (TgOut o : p.outs) {
+          if (o.n_parts > 1) o.part_off += part_base;
+          b.outs.push_back(o);
+        }
+        for (int r : p.red) b.red.push_back(r + o0);
+        append(&b.chunks, p.chunks);
+        part_base += p.scratch_need;
+        b.max_npad = std::max(b.max_npad, p.max_npad);
+        b.flops += p.flops;
+      }
+      b.scratch_need = part_base;
+      scratch = std::max(scratch, part_base);
+      b.upload(e0->stream_);
+    }
+    device_alloc((void**)&g->tg_scratch, (size_t)std::max(scratch, 1LL) * sizeof(float), "batched partial sums");
   } else {
     for (int m : members) {
       Engine* e = es_[m];
@@ -160,6 +200,21 @@ int BatchRunner::launch(Grouped& g) {
     if (rc) e0->err_ = "tensor-core H_eff: tile shape outside the supported range";
     return rc;
   }
+  if (g.tg) {
+    const int elem = e0->precision_ == PREC_BF16 ? 2 : 4;
+    const int split = e0->precision_ == PREC_TF32X3 ? 1 : 0;
+    for (int i = 0; i < 3; ++i) {
+      TgPlan& p = g.tgs[i];
+      const int rc = launch_tg_gemm(elem, split, p.d_tiles, (int)p.tiles.size(), p.d_outs, p.d_chunks, p.max_npad,
+                                    g.tg_scratch, p.d_red, (int)p.red.size(), e0->d_err_, s, e0->wait_polls);
+      if (rc) {
+        e0->err_ = "tensor-core contraction: output width outside the supported range";
+        return rc;
+      }
+    }
+    g.launched = true;
+    return 0;
+  }
   for (auto& z : g.zero) cudaMemsetAsync(z.first, 0, z.second * sizeof(double), s);
   for (int i = 0; i < 3; ++i) {
     const int rc = e0->launch_kplan(g.st[i], g.fp32, true);
@@ -201,6 +256,7 @@ int BatchRunner::product(int node, const std::vector<int>& active) {
   bool tuned = true;
   for (const KPlan& p : g->st)
     if (!p.outs.empty() && p.shape[g->fp32] < 0 && e0->forced_shape_ < 0) tuned = false;
+  if (g->tg && !g->launched) tuned = false;   // first launch eager (one-time kernel set-up on the host)
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   const bool capturable = use_graphs_ && tuned && s != nullptr &&
                           cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
@@ -344,7 +400,11 @@ int BatchRunner::optimize(int node, double tol, int max_krylov, std::vector<Swee
     for (int b = 0; b < B; ++b) {
       double e = 0.0, r = 0.0;
       int it = 0;
-      if ((rc = es_[b]->lanczos(node, tol, max_krylov, false, 50, &e, &r, &it))) return rc;
+      // the residual correction with float-float products, as in an unbatched update
+      es_[b]->ff_products_ = true;
+      rc = es_[b]->lanczos(node, tol, max_krylov, false, 50, &e, &r, &it);
+      es_[b]->ff_products_ = false;
+      if (rc) return rc;
       energy[b] = e;
       res[b] = r;
       iters[b] = it;

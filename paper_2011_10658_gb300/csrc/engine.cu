@@ -32,6 +32,7 @@ constexpr double kQrFallback = 1e-6;
 constexpr double kQrDependent = 1e-9;
 constexpr double kQrAccept = 0.5;
 constexpr long long kZPoolBudget = 64LL << 20;   // doubles in the Z work pool for operator updates
+constexpr int kOzAmax = 4000;                    // device scalar slot: max |T| of a digit-plane split
 }  // namespace
 
 // ------------------------------------------------------------------ Layout
@@ -291,6 +292,14 @@ void TcPlan::release() {
   for (size_t& c : cap) c = 0;
 }
 
+void OzPlan::release() {
+  void* ptrs[4] = {d_tiles, d_jobs, d_outs, d_sums};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  d_tiles = nullptr; d_jobs = nullptr; d_outs = nullptr; d_sums = nullptr;
+  for (size_t& c : cap) c = 0;
+}
+
 void TgPlan::upload(cudaStream_t s) {
   grow_upload(d_tiles, cap[0], tiles, s);
   grow_upload(d_outs, cap[1], outs, s);
@@ -500,7 +509,7 @@ int KPlan::candidates(int* out) const {
 // (the last two: 16x64 and 64x16).
 int Engine::launch_kplan(KPlan& pl, int fp32, bool tune) {
   if (pl.outs.empty()) return 0;
-  const int mode = fp32 ? 1 : 0;
+  const int mode = fp32;   // 0 FP64, 1 FP32, 2 float-float
   int shape = forced_shape_ >= 0 ? forced_shape_ : pl.shape[mode];
   if (shape < 0 && !tune) {   // one-off plans: the least padded shape
     int cand[KS_COUNT];
@@ -677,6 +686,9 @@ Engine::~Engine() {
     cudaFree(kv.second.status);
   }
   tg_cache_.clear();
+  oz_cache_.clear();
+  if (oz_planes_) cudaFree(oz_planes_);
+  if (oz_partial_) cudaFree(oz_partial_);
   if (tg_pool_) cudaFree(tg_pool_);
   if (tg_scratch_) cudaFree(tg_scratch_);
   if (ident_) cudaFree(ident_);
@@ -1251,7 +1263,16 @@ int Engine::compute_up(int node) {
   for (int c = 0; c < N_CLASSES; ++c) cudaMemsetAsync(out.H[c], 0, dd * sizeof(double), stream_);
   for (auto& kv : out.term) cudaMemsetAsync(kv.second.ptr, 0, dd * sizeof(double), stream_);
   int rc = 0;
-  if (bottom) {
+  if (bottom && precision_ != PREC_FP64) {
+    // mixed states: FP64-accurate digit-plane products on the tensor cores
+    std::vector<std::pair<double*, double>> oc_terms;
+    std::vector<int> oc_keys;
+    for (const Contrib& c : cs) {
+      oc_terms.push_back({c.O, c.alpha});
+      oc_keys.push_back(c.term);
+    }
+    rc = compute_up_oz(node, oc_terms, oc_keys, out);
+  } else if (bottom) {
     // term contributions through row maps: O[c', c] += alpha sum_r T[r, c'] val(r) T[map(r), c]
     KPlan* pl = cached_plan(PK_UP, node, 0, 0, [&](KPlan& w) {
       auto add_map = [&](double* O, double alpha, const std::vector<RowMap>& maps) {
@@ -1333,13 +1354,198 @@ int Engine::compute_up(int node) {
           plan_contract_but(*p[2], L, T, lays[shift], Z, 2, jb.O, dim, jb.alpha);
         }
       });
-      for (int i = 0; i < 3 && rc == 0; ++i) rc = launch_plan(st[i]);
+      for (int i = 0; i < 3 && rc == 0; ++i) rc = launch_plan(st[i], ops_mode());
     }
   }
   // Htot = sum of classes
   cudaMemsetAsync(out.Htot, 0, dd * sizeof(double), stream_);
   for (int c = 0; c < N_CLASSES; ++c) launch_add_scaled(out.H[c], out.Htot, dd, 1.0, stream_);
   return rc;
+}
+
+// Operators of the bond above bottom node `node` on the BF16 tensor cores
+// at FP64-level accuracy (digit planes, kernels_oz.cu): every term with a
+// signed row map contributes O[oc-block, ic-block] += alpha T_oc^T T_ic[map];
+// each site Hamiltonian of a coupling class (a diagonal row scaling) is
+// split into one 0/1 row selection per distinct value v, with alpha = v.
+// terms[i] / keys[i]: output operator and coefficient of term keys[i].
+int Engine::compute_up_oz(int node, const std::vector<std::pair<double*, double>>& terms,
+                          const std::vector<int>& keys, BondOps& out) {
+  const Layout& L = layout_[node];
+  const Sectors& P = L.leg[2];
+  const int dim = P.total();
+  const int ns = (int)P.q.size();
+  if (!oz_planes_) {
+    device_alloc((void**)&oz_planes_, (size_t)nmax_ * 16, "digit planes");
+    track(oz_planes_, (size_t)nmax_ * 16);
+  }
+  auto it = oz_cache_.find(node);
+  if (it == oz_cache_.end()) {
+    std::unique_ptr<OzPlan> pl(new OzPlan);
+    OzPlan& op = *pl;
+    struct J { const int* map; int oc, ic; double* O; double alpha; long long nnz; };
+    std::vector<J> js;
+    for (size_t i = 0; i < terms.size(); ++i) {
+      const std::vector<RowMap>& maps = rowmap(node, keys[i]);
+      for (int oc = 0; oc < ns; ++oc) {
+        const RowMap& rm = maps[oc];
+        if (rm.src_sector < 0 || L.sec_rows[oc] == 0) continue;
+        if (rm.val) { err_ = "digit-plane operator update: valued row map of a term"; return -7; }
+        js.push_back({rm.map, oc, rm.src_sector, terms[i].first, terms[i].second, rm.nnz});
+      }
+    }
+    // site Hamiltonians per leg and class: 0/1 row selections per distinct value
+    const int sites[2] = {leg_site(node, 0), leg_site(node, 1)};
+    for (int leg = 0; leg < 2; ++leg) {
+      const int st = sites[leg];
+      for (int cl = 0; cl < N_CLASSES; ++cl) {
+        double diag[kLocalDim];
+        for (int r = 0; r < kLocalDim; ++r) diag[r] = 0.0;
+        for (const Term& t : terms_) {
+          if (t.ops.size() != 1 || t.ops[0].first != st || t.cls != cl) continue;
+          const SiteOp* so = site_op(lat_.parity(st), t.ops[0].second);
+          for (int r = 0; r < kLocalDim; ++r)
+            if (so->src[r] == r) diag[r] += t.coef * so->val[r];
+        }
+        std::vector<double> vals;
+        for (int r = 0; r < kLocalDim; ++r)
+          if (diag[r] != 0.0 && std::find(vals.begin(), vals.end(), diag[r]) == vals.end()) vals.push_back(diag[r]);
+        for (double v : vals) {
+          for (int oc = 0; oc < ns; ++oc) {
+            const int rows = L.sec_rows[oc];
+            if (rows == 0) continue;
+            std::vector<int> m(rows, -1);
+            long long nnz = 0;
+            for (const Layout::Blk& b : L.blk) {
+              if (b.ic != oc) continue;
+              const int a_off = L.leg[0].offset(b.ia), b_off = L.leg[1].offset(b.ib);
+              for (int a = 0; a < b.da; ++a)
+                for (int c = 0; c < b.db; ++c) {
+                  const int idx = leg == 0 ? a_off + a : b_off + c;
+                  if (diag[idx] == v) {
+                    const int r = b.row0 + a * b.db + c;
+                    m[r] = r << 1;
+                    ++nnz;
+                  }
+                }
+            }
+            if (!nnz) continue;
+            int* dm = (int*)dalloc((size_t)rows * sizeof(int));
+            cudaMemcpyAsync(dm, m.data(), (size_t)rows * sizeof(int), cudaMemcpyHostToDevice, stream_);
+            js.push_back({dm, oc, oc, out.H[cl], v, nnz});
+          }
+        }
+      }
+    }
+    cudaStreamSynchronize(stream_);
+    // tiles: jobs of one output sector share the T_oc operand; up to four
+    // jobs of at most 32 columns per CTA; the rows of the sector are cut
+    // into K ranges (multiples of 32) so that the launch fills the GPU
+    std::vector<int> order(js.size());
+    for (size_t i = 0; i < js.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return js[a].oc < js[b].oc; });
+    int maxd = 0;
+    for (int i = 0; i < ns; ++i) maxd = std::max(maxd, P.dim[i]);
+    const int slot = maxd <= 32 ? 32 : (maxd <= 64 ? 64 : 128);
+    op.npad = maxd <= 32 ? 32 : 64;
+    if (maxd > 64) { err_ = "digit-plane operator update: sector dimension above 64"; return -7; }
+    long long total_groups = 0;
+    std::vector<std::vector<int>> groups;   // per tile-group: job indices (same oc)
+    for (size_t i = 0; i < order.size();) {
+      std::vector<int> g;
+      const int oc = js[order[i]].oc;
+      while (i < order.size() && js[order[i]].oc == oc && (int)g.size() < 128 / slot) g.push_back(order[i++]);
+      groups.push_back(g);
+      total_groups += 1;
+    }
+    long long row_work = 0;
+    for (const auto& g : groups) row_work += L.sec_rows[js[g[0]].oc];
+    // about 8 CTAs' worth of K ranges per SM over the whole launch
+    const long long target = 8LL * 152;
+    long long kr = std::max<long long>(256, (row_work + target - 1) / target);
+    kr = (kr + 31) / 32 * 32;
+    long long part_off = 0;
+    std::vector<int> job_parts(js.size(), 1);
+    std::vector<long long> job_off(js.size(), 0);
+    for (const auto& g : groups) {
+      const int oc = js[g[0]].oc;
+      const int rows = L.sec_rows[oc];
+      const int parts = (int)((rows + kr - 1) / kr);
+      const int tile0 = (int)op.tiles.size();
+      for (int p = 0; p < parts; ++p) {
+        OzTile t{};
+        t.b_off = L.sec_off[oc];
+        t.b_ld = P.dim[oc];
+        t.n = P.dim[oc];
+        t.r0 = (int)(p * kr);
+        t.r1 = (int)std::min<long long>(rows, (p + 1) * kr);
+        t.job_begin = (int)op.jobs.size();
+        t.job_end = t.job_begin + (int)g.size();
+        t.slot = slot;
+        t.part = p;
+        op.tiles.push_back(t);
+      }
+      (void)tile0;
+      for (int j : g) {
+        OzJob oj{};
+        oj.map = js[j].map;
+        oj.a_off = L.sec_off[js[j].ic];
+        oj.a_ld = P.dim[js[j].ic];
+        oj.cols = P.dim[js[j].ic];
+        oj.part_off = part_off;
+        job_off[j] = part_off;
+        job_parts[j] = parts;
+        part_off += (long long)parts * oj.cols * P.dim[oc];
+        op.jobs.push_back(oj);
+        op.flops += 2.0 * (double)js[j].nnz * P.dim[oc] * P.dim[js[j].ic];
+      }
+    }
+    op.partial_elems = part_off;
+    // outputs: one per operator block, its jobs in job order
+    std::map<std::pair<double*, long long>, std::vector<int>> by_block;
+    for (size_t j = 0; j < js.size(); ++j) {
+      const long long boff = (long long)P.offset(js[j].oc) * dim + P.offset(js[j].ic);
+      by_block[{js[j].O, boff}].push_back((int)j);
+    }
+    for (auto& kv : by_block) {
+      const J& j0 = js[kv.second[0]];
+      OzOut o{};
+      o.O = kv.first.first + kv.first.second;
+      o.ld = dim;
+      o.rows = P.dim[j0.oc];
+      o.cols = P.dim[j0.ic];
+      o.sum_begin = (int)op.sums.size();
+      for (int j : kv.second) {
+        OzSum sm{};
+        sm.off = job_off[j];
+        sm.part_stride = (long long)P.dim[js[j].ic] * P.dim[js[j].oc];
+        sm.n_parts = job_parts[j];
+        sm.alpha = js[j].alpha;
+        op.sums.push_back(sm);
+      }
+      o.sum_end = (int)op.sums.size();
+      op.outs.push_back(o);
+    }
+    grow_upload(op.d_tiles, op.cap[0], op.tiles, stream_);
+    grow_upload(op.d_jobs, op.cap[1], op.jobs, stream_);
+    grow_upload(op.d_outs, op.cap[2], op.outs, stream_);
+    grow_upload(op.d_sums, op.cap[3], op.sums, stream_);
+    if (op.partial_elems > oz_partial_elems_) {
+      cudaStreamSynchronize(stream_);
+      if (oz_partial_) { untrack(oz_partial_); cudaFree(oz_partial_); }
+      oz_partial_elems_ = op.partial_elems + op.partial_elems / 4;
+      device_alloc((void**)&oz_partial_, oz_partial_elems_ * sizeof(double), "digit-plane partial sums");
+      track(oz_partial_, oz_partial_elems_ * sizeof(double));
+    }
+    it = oz_cache_.emplace(node, std::move(pl)).first;
+  }
+  OzPlan& op = *it->second;
+  launch_oz_slice(T_[node], L.size, d_scal_ + kOzAmax, oz_planes_, stream_);
+  const int rc = launch_oz_gram(op.d_tiles, (int)op.tiles.size(), op.d_jobs, oz_planes_, op.npad, oz_partial_,
+                                op.d_outs, (int)op.outs.size(), op.d_sums, d_err_, stream_, wait_polls);
+  if (rc) { err_ = "digit-plane operator update: unsupported shape"; return rc; }
+  ops_flops_ += op.flops;
+  return check(cudaGetLastError(), "digit-plane operator update") ? 0 : -3;
 }
 
 // Environment operators of the bond above `node`, from its parent's tensor
@@ -1437,7 +1643,7 @@ int Engine::compute_down(int node) {
         plan_contract_but(*p[2], L, T, lays[shift], Z, leg, jb.O, dim, jb.alpha);
       }
     });
-    for (int i = 0; i < 3 && rc == 0; ++i) rc = launch_plan(st[i]);
+    for (int i = 0; i < 3 && rc == 0; ++i) rc = launch_plan(st[i], ops_mode());
   }
   cudaMemsetAsync(out.Htot, 0, dd * sizeof(double), stream_);
   for (int c = 0; c < N_CLASSES; ++c) launch_add_scaled(out.H[c], out.Htot, dd, 1.0, stream_);
@@ -1487,10 +1693,11 @@ int Engine::move_path(int target) {
     tc_w_node_ = -1;   // environment operators change with the move
     if (profiling_) ev_begin(&e0);
     ops_flops_ = 0.0;
+    const bool bottom_up = leg_c == 2 && nodes_[c].child_kind[0] == 0;
     if (leg_c == 2) rc = compute_up(c);
     else rc = compute_down(t);
     if (rc) return rc;
-    if (profiling_) ev_end(e0, KC_MOVE_OPS, ops_flops_, ops_flops_, 0);
+    if (profiling_) ev_end(e0, bottom_up ? KC_MOVE_OPS_BOTTOM : KC_MOVE_OPS, ops_flops_, ops_flops_, 0);
   }
   return check(cudaGetLastError(), "move") ? 0 : -3;
 }
@@ -1791,7 +1998,7 @@ int Engine::apply_heff(const double* x, double* y, int cls) {
     cudaMemsetAsync(zpool_, 0, hp->z_elems * sizeof(double), stream_);
   }
   for (int i = 0; i < 3; ++i) {
-    const int rc = launch_kplan(hp->st[i], 0, true);
+    const int rc = launch_kplan(hp->st[i], ff_products_ && cls < 0 ? 2 : 0, true);
     if (rc) return rc;
   }
   if (profiling_) ev_end(e0, bottom ? KC_HEFF_SIMT_BOTTOM : KC_HEFF_SIMT_UPPER, hp->flops, hp->flops, 0.0);
@@ -2143,6 +2350,7 @@ Engine::TgHeff* Engine::tg_plans(int node) {
   if ((long long)nz * zsize > tg_pool_elems_) {
     cudaStreamSynchronize(stream_);   // cached plans point into the old pool
     tg_cache_.clear();
+    ++gen_;
     if (tg_pool_) { untrack(tg_pool_); cudaFree(tg_pool_); tg_pool_ = nullptr; }
     tg_pool_elems_ = (long long)std::max(nz, 1) * zsize + zsize;
     device_alloc((void**)&tg_pool_, tg_pool_elems_ * sizeof(float), "tensor-core intermediates");
@@ -2155,6 +2363,7 @@ Engine::TgHeff* Engine::tg_plans(int node) {
   if (dmax > ident_dim_) {
     cudaStreamSynchronize(stream_);   // cached plans point at the old identity
     tg_cache_.clear();
+    ++gen_;
     if (ident_) { untrack(ident_); cudaFree(ident_); }
     ident_dim_ = dmax;
     device_alloc((void**)&ident_, (size_t)dmax * dmax * sizeof(double), "identity blocks");
@@ -2614,7 +2823,10 @@ int Engine::optimize_node(int node, double tol, int max_krylov, SweepStats* st, 
       return -6;
     }
   }
+  // the FP64 residual correction: float-float products in a mixed state
+  ff_products_ = mixed_node(node);
   rc = lanczos(node, tol, max_krylov, false, 50, &energy, &res, &iters);
+  ff_products_ = false;
   if (rc) return rc;
   last_lanczos_iters = iters;
   last_mixed_iters = mixed_iters;

@@ -88,9 +88,9 @@ struct KPlan {
   long long k_part = 4096;
   double flops = 0.0;   // 2 M N K over the GEMM chunks (set by finalize)
   KVariant var[KS_COUNT];
-  int shape[2] = {-1, -1};    // tuned tile shape per arithmetic, -1 while tuning
-  int trials[2] = {0, 0};
-  cudaEvent_t tev[2][KS_COUNT][2][2] = {};   // [arithmetic][shape][repeat][start, stop]
+  int shape[3] = {-1, -1, -1};    // tuned tile shape per arithmetic (FP64, FP32, float-float), -1 while tuning
+  int trials[3] = {0, 0, 0};
+  cudaEvent_t tev[3][KS_COUNT][2][2] = {};   // [arithmetic][shape][repeat][start, stop]
   void clear() {
     chunks.clear(); outs.clear(); out_chunks.clear(); out_index.clear(); current = -1; flops = 0.0;
     for (KVariant& v : var) v.ready = false;
@@ -186,6 +186,24 @@ struct TgPlan {
   ~TgPlan() { release(); }
 };
 
+// Digit-plane (FP64-accurate tensor-core) operator update of a bottom node.
+struct OzPlan {
+  std::vector<OzTile> tiles;
+  std::vector<OzJob> jobs;
+  std::vector<OzOut> outs;
+  std::vector<OzSum> sums;
+  OzTile* d_tiles = nullptr;
+  OzJob* d_jobs = nullptr;
+  OzOut* d_outs = nullptr;
+  OzSum* d_sums = nullptr;
+  size_t cap[4] = {0, 0, 0, 0};
+  long long partial_elems = 0;
+  int npad = 32;
+  double flops = 0.0;   // algorithmic: 2 x mapped rows x chi_out x chi_in per job
+  void release();
+  ~OzPlan() { release(); }
+};
+
 // Per kernel-class timing of launches on the engine stream (CUDA events).
 // SIMT classes run FP64, or FP32 inside the low-precision phase of a mixed state.
 // KC_MOVE and KC_LANCZOS time whole phases (centre moves with QR and
@@ -193,8 +211,9 @@ struct TgPlan {
 enum KernelClass {
   KC_TC_HEFF = 0, KC_HEFF_SIMT_BOTTOM = 1, KC_HEFF_SIMT_UPPER = 2, KC_MOVE = 3, KC_LANCZOS = 4,
   KC_MOVE_QR = 5,    // per bond: QR of the departing tensor and R absorption (FP64)
-  KC_MOVE_OPS = 6,   // per bond: renormalized / environment operator update (FP64)
-  KC_COUNT = 7
+  KC_MOVE_OPS = 6,   // per bond: renormalized / environment operator update at an upper node
+  KC_MOVE_OPS_BOTTOM = 7,   // per bond: operator update leaving a bottom node upwards
+  KC_COUNT = 8
 };
 struct KernelTiming {
   double ms = 0.0;
@@ -373,6 +392,12 @@ class Engine {
   double* ident_ = nullptr;
   int ident_dim_ = 0;
   TgHeff* tg_plans(int node);
+  std::map<int, std::unique_ptr<OzPlan>> oz_cache_;
+  void* oz_planes_ = nullptr;
+  double* oz_partial_ = nullptr;
+  long long oz_partial_elems_ = 0;
+  int compute_up_oz(int node, const std::vector<std::pair<double*, double>>& terms, const std::vector<int>& keys,
+                    BondOps& out);
   int apply_heff_tg();
   int tc_w_node_ = -1;          // node whose environment blocks are staged
   void clear_tc_cache();
@@ -465,6 +490,10 @@ class Engine {
   bool lz_converged(int slot, double tol, double* theta, double* res) const;
   friend class BatchRunner;
   bool use_mixed_ = false;   // current matvec precision inside lanczos
+  // products of a mixed state's FP64 residual correction run in float-float
+  // arithmetic (FP64-level accuracy on the FP32 pipes)
+  bool ff_products_ = false;
+  int ops_mode() const { return precision_ != PREC_FP64 ? 2 : 0; }
 };
 
 }  // namespace qed

@@ -62,9 +62,11 @@ inline int kc_shape_n(int shape) {
   return n[shape];
 }
 
-// fp32 != 0: same contraction with FP32 multiply-accumulate (operands
-// rounded to FP32 on load, results stored as FP64).  shape: the tile shape
-// the tiles were cut with.
+// fp32 = 1: same contraction with FP32 multiply-accumulate (operands
+// rounded to FP32 on load, results stored as FP64); fp32 = 2: float-float
+// arithmetic on the FP32 pipes (operands split into two FP32 numbers, about
+// 48 significant bits; FP64-level accuracy).  shape: the tile shape the
+// tiles were cut with.
 void launch_kc_gemm(const KTile* tiles, int n_tiles, const KOutput* outs, const KChunk* chunks,
                     double* scratch, cudaStream_t s, int fp32 = 0, int shape = KS_32);
 void launch_kc_reduce(const KOutput* outs, int n_outs, const int* red_list, int n_red, double* scratch,
@@ -226,6 +228,51 @@ int tg_stage_bytes(int elem, int split, int max_npad, int* a_bytes, int* b_bytes
 int launch_tg_gemm(int elem, int split, const TgTile* tiles, int n_tiles, const TgOut* outs, const TgChunk* chunks,
                    int max_npad, float* scratch, const int* red_list, int n_red, int* err, cudaStream_t s,
                    long long polls = -1);
+
+// ---- FP64-accurate contractions on the BF16 tensor cores (digit planes) ----
+constexpr int kOzDigits = 5;   // balanced base-256 digits per FP64 entry (about 2^-39 of the max)
+// planes (16 bytes per entry, 8 BF16 planes of which kOzDigits are used)
+// <- x[0..n), relative to 2^E >= max |x| (max |x| written to *amax).
+void launch_oz_slice(const double* x, long long n, double* amax, void* planes, cudaStream_t s);
+// Job: for one term and output sector, rows (c < cols) of the source sector
+// matrix (at a_off, row stride a_ld, in planes) selected by map (sign-encoded
+// source row per output row; NULL = identity).  Its FP64 partial blocks
+// [part][c][c'] start at part_off.
+struct OzJob {
+  const int* map;
+  long long a_off;
+  long long part_off;
+  int a_ld;
+  int cols;
+};
+// CTA: jobs [job_begin, job_end) stacked in slots of `slot` MMA rows, against
+// output sector rows [r0, r1) (at b_off, row stride b_ld, n columns c'),
+// writing partial slot `part` of each job.
+struct OzTile {
+  long long b_off;
+  int b_ld, n;
+  int r0, r1;
+  int job_begin, job_end;
+  int slot;
+  int part;
+};
+// One operator block O[c', c] (ld) += sum over its entries of alpha * the
+// sum of that job's partial blocks.
+struct OzSum {
+  long long off;          // job's part_off
+  long long part_stride;  // cols * n
+  int n_parts;
+  double alpha;
+};
+struct OzOut {
+  double* O;
+  int ld;
+  int rows, cols;         // c' (output sector) x c (source sector)
+  int sum_begin, sum_end;
+};
+// npad: MMA width (32 or 64, >= every tile's n).  err: set if a wait timed out.
+int launch_oz_gram(const OzTile* tiles, int n_tiles, const OzJob* jobs, const void* planes, int npad, double* partial,
+                   const OzOut* outs, int n_outs, const OzSum* sums, int* err, cudaStream_t s, long long polls = -1);
 
 // mode 0: plain (BF16 or FP32 by elem); mode 1: split x rows [hi | lo] of
 // width 2 kpad; mode 2: split W rows [hi | lo] of width 2 kpad.  hi is

@@ -53,6 +53,61 @@ __device__ __forceinline__ double f2d_bits(float f) {
   return __longlong_as_double((long long)(sign | ((unsigned long long)(e - 127 + 1023) << 52) | (frac << 29)));
 }
 
+// ---- float-float arithmetic: a value hi + lo held in two FP32 numbers
+// (about 48 significant bits), with products and sums made error-free by
+// FMA (Dekker's TwoProduct) and Knuth's TwoSum.  GB300 runs FP32 at many
+// times its FP64 rate, so a float-float multiply-add (about a dozen FP32
+// instructions) outruns one FP64 FMA while keeping FP64-level accuracy for
+// these contractions.
+struct ff {
+  float hi, lo;
+  __device__ __forceinline__ ff() {}
+  __device__ __forceinline__ explicit ff(float h) : hi(h), lo(0.f) {}
+  __device__ __forceinline__ ff(float h, float l) : hi(h), lo(l) {}
+};
+
+__device__ __forceinline__ ff ff_norm(float s, float e) {
+  const float h = s + e;
+  return ff(h, e - (h - s));
+}
+
+__device__ __forceinline__ ff operator*(ff a, ff b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return ff_norm(p, e);
+}
+
+__device__ __forceinline__ ff operator+(ff a, ff b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float err = (a.hi - (s - bb)) + (b.hi - bb) + a.lo + b.lo;
+  return ff_norm(s, err);
+}
+
+__device__ __forceinline__ ff& operator*=(ff& a, ff b) { a = a * b; return a; }
+__device__ __forceinline__ ff& operator+=(ff& a, ff b) { a = a + b; return a; }
+
+// c + a b with the product's error and the sum's error kept in lo
+__device__ __forceinline__ ff kc_fma(ff a, ff b, ff c) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const float s = c.hi + p;
+  const float bb = s - c.hi;
+  const float err = (c.hi - (s - bb)) + (p - bb);
+  return ff(s, c.lo + e + err);
+}
+
+__device__ __forceinline__ double kc_fma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float kc_fma(float a, float b, float c) { return fmaf(a, b, c); }
+
+// FP64 -> float-float on the integer pipes: hi = the double cut to 24
+// significant bits, lo = the remaining 29 fraction bits (rounded to 24)
+__device__ __forceinline__ ff d2ff(double d);
+
 template <typename T>
 __device__ __forceinline__ T to_t(double v);
 template <>
@@ -60,12 +115,33 @@ __device__ __forceinline__ double to_t<double>(double v) { return v; }
 template <>
 __device__ __forceinline__ float to_t<float>(double v) { return d2f_bits(v); }
 
+template <>
+__device__ __forceinline__ ff to_t<ff>(double v) { return d2ff(v); }
+
+__device__ __forceinline__ ff d2ff(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const float hi = d2f_bits(__longlong_as_double((long long)(b & ~((1ull << 29) - 1ull))));
+  const int e = (int)((b >> 52) & 0x7ff);
+  const unsigned low = (unsigned)(b & ((1ull << 29) - 1ull));
+  float lo = 0.f;
+  if (e != 0 && e != 0x7ff && low) {
+    // low x 2^(e - 1075): convert the integer, then move its exponent
+    const float f = (float)low;
+    const int ex = (int)((__float_as_uint(f) >> 23) & 0xff) + (e - 1075);
+    if (ex > 0) lo = __uint_as_float((__float_as_uint(f) & 0x807fffffu) | ((unsigned)ex << 23));
+    if (b >> 63) lo = -lo;
+  }
+  return ff(hi, lo);
+}
+
 template <typename T>
 __device__ __forceinline__ double to_d(T v);
 template <>
 __device__ __forceinline__ double to_d<double>(double v) { return v; }
 template <>
 __device__ __forceinline__ double to_d<float>(float v) { return f2d_bits(v); }
+template <>
+__device__ __forceinline__ double to_d<ff>(ff v) { return f2d_bits(v.hi) + f2d_bits(v.lo); }
 
 // Row maps are sign-encoded: -1 = zero row, otherwise (row << 1) | negate.
 // Arithmetic in T (FP64, or FP32 with the operands converted first).
@@ -152,7 +228,7 @@ __global__ void __launch_bounds__(THREADS) kc_gemm_kernel(const KTile* __restric
 #pragma unroll
         for (int i = 0; i < TM; ++i)
 #pragma unroll
-          for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
+          for (int j = 0; j < TN; ++j) acc[i][j] = kc_fma(a[i], bv[j], acc[i][j]);
       }
       __syncthreads();
     }
@@ -800,8 +876,10 @@ void launch_kc_gemm(const KTile* tiles, int n_tiles, const KOutput* outs, const 
     case KS_64x16: QED_KC(T, 64, 16); break; \
     default: QED_KC(T, 32, 32); break;      \
   }
-  if (fp32) {
+  if (fp32 == 1) {
     QED_KC_ALL(float)
+  } else if (fp32 == 2) {
+    QED_KC_ALL(ff)
   } else {
     QED_KC_ALL(double)
   }
