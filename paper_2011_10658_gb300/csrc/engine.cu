@@ -650,7 +650,7 @@ Engine::Engine(const Params& p, int chi, uint64_t seed, int precision, cudaStrea
   grad_b_ = (double*)dalloc(nmax_ * sizeof(double));
   grad_c_ = (double*)dalloc(nmax_ * sizeof(double));
   d_scal_ = (double*)dalloc(8192 * sizeof(double));
-  d_partial_ = (double*)dalloc(304 * (kMaxKrylov + 2) * sizeof(double));
+  d_partial_ = (double*)dalloc(1216 * (kMaxKrylov + 2) * sizeof(double));
   d_err_ = (int*)dalloc(4 * sizeof(int));   // [0] tensor-core wait flag, [1] thick-restart count, [2] non-finite flag
   if (!check(cudaStreamCreateWithFlags(&aux_, cudaStreamNonBlocking), "side stream")) throw std::runtime_error(err_);
   for (int i = 0; i <= kMaxKrylov; ++i) {
@@ -2606,7 +2606,7 @@ int Engine::lanczos(int node, double tol, int max_krylov, bool mixed, int max_re
 // Gram-Schmidt coefficients, norms; a thick restart's k x keep combination.
 namespace {
 constexpr int kAlpha = 0, kBeta = 128, kSvec = 256, kOut = 384, kCoef = 512, kNrm2 = 640, kNrmPre = 641,
-              kNrmMid = 642, kCmat = 1024;
+              kNrmMid = 642, kCmat = 1024, kC1 = 2048, kC2 = 2304, kMid = 2500, kNrmSecond = 2501;
 }
 
 int Engine::lz_prepare(int kmax) {
@@ -2634,32 +2634,25 @@ void Engine::lz_start(int node) {
   launch_scale_inv_sqrt(tmp_, V_, n, d_scal_ + kNrm2, stream_);
 }
 
-// With y_out_ = H_eff v_j: alpha_j, the three-term recurrence, full
-// reorthogonalisation (one classical Gram-Schmidt pass, a second only if the
-// first removed more than half of ||w||^2) and beta_j = ||w||.
+// With y_out_ = H_eff v_j: alpha_j, the three-term recurrence folded into the
+// first classical Gram-Schmidt pass against all j + 1 basis vectors (the
+// coefficients come from the reduced vector, as in a separate three-term
+// step, so that rounding stays relative to beta_j and not to alpha_j), a
+// second pass only if the first removed more than half of ||w'||^2 (Daniel-
+// Gragg-Kaufman-Stewart, decided on the device), beta_j = ||w|| and
+// v_{j+1} = w / beta_j (column kmax holds the residual vector of a full
+// cycle).  Eleven launches.
 void Engine::lz_iteration(int j, long long n) {
-  const long long ld = nmax_;
-  double* alpha = d_scal_ + kAlpha;
-  double* beta = d_scal_ + kBeta;
-  double* coef = d_scal_ + kCoef;
-  double* vj = V_ + j * ld;
-  launch_dot(vj, y_out_, n, d_partial_, alpha + j, stream_);
-  launch_axpby(vj, y_out_, n, alpha + j, 0.0, -1.0, nullptr, 1.0, stream_);
-  if (j > 0) launch_axpby(V_ + (j - 1) * ld, y_out_, n, beta + (j - 1), 0.0, -1.0, nullptr, 1.0, stream_);
-  launch_dot(y_out_, y_out_, n, d_partial_, d_scal_ + kNrmPre, stream_);
-  launch_multidot(V_, ld, j + 1, y_out_, n, d_partial_, coef, stream_);
-  launch_multiaxpy(V_, ld, j + 1, coef, y_out_, n, stream_);
-  launch_dot(y_out_, y_out_, n, d_partial_, d_scal_ + kNrmMid, stream_);
-  launch_multidot(V_, ld, j + 1, y_out_, n, d_partial_, coef, stream_, d_scal_ + kNrmMid, d_scal_ + kNrmPre,
-                  kReorthRatio);
-  launch_multiaxpy(V_, ld, j + 1, coef, y_out_, n, stream_, d_scal_ + kNrmMid, d_scal_ + kNrmPre, kReorthRatio);
-  launch_dot(y_out_, y_out_, n, d_partial_, d_scal_ + kNrm2, stream_);
-  launch_sqrt(d_scal_ + kNrm2, beta + j, stream_);
+  launch_lz_reorth(V_, nmax_, j + 1, y_out_, n, d_partial_, d_scal_ + kC1, d_scal_ + kC2, d_scal_ + kMid,
+                   d_scal_ + kNrmSecond, kReorthRatio, d_scal_ + kAlpha + j, j > 0 ? d_scal_ + kBeta + j - 1 : nullptr,
+                   d_scal_ + kBeta + j, d_scal_ + kNrm2, V_ + (long long)(j + 1) * nmax_, stream_,
+                   precision_ != PREC_FP64 ? 1 : 0);
 }
 
-// v_{j+1} = w / beta_j (column kmax holds the residual vector of a full cycle)
+// v_{j+1} is written by lz_iteration.
 void Engine::lz_next_vector(int j, long long n) {
-  launch_scale_inv_sqrt(y_out_, V_ + (long long)(j + 1) * nmax_, n, d_scal_ + kNrm2, stream_);
+  (void)j;
+  (void)n;
 }
 
 // Thick restart after a full cycle of k vectors (see lanczos_restart_kernel);

@@ -87,6 +87,20 @@ void launch_multiaxpy(const double* Q, long long ldq, int k, const double* c, do
                       double ratio = 0.0);
 // x = sum_j c[j] Q_j
 void launch_combine(const double* Q, long long ldq, int k, const double* c, double* x, long long n, cudaStream_t s);
+// One Lanczos step after y = H v_{k-1} (V holds v_0 .. v_{k-1}, columns of
+// stride ldq): alpha_j = v_j . y, the three-term residual
+// w' = y - alpha_j v_j - beta_{j-1} v_{j-1} (beta_prev, unused for k = 1),
+// classical Gram-Schmidt of w' against all k vectors (c1 = V^T w', w'.w' in
+// c1[k]), a second pass into c2 when the Daniel-Gragg-Kaufman-Stewart test
+// asks for it (decided on the device), then beta_j = |w|, *nrm_out = |w|^2
+// and v_next = w / |w|.  Eleven launches; partial holds 1216 x (k + 1)
+// doubles; c1 k + 1 and c2 k doubles; k <= 128.  ff_arith != 0: the dots and
+// updates in float-float arithmetic on the FP32 pipes (about 2^-44 relative
+// rounding per operation; the data stay FP64).
+void launch_lz_reorth(const double* V, long long ldq, int k, double* y, long long n, double* partial, double* c1,
+                      double* c2, double* mid, double* nrm_second, double ratio, double* alpha_j,
+                      const double* beta_prev, double* beta_j, double* nrm_out, double* v_next, cudaStream_t s,
+                      int ff_arith = 0);
 // out[0] = sqrt(max(in[0], 0))
 void launch_sqrt(const double* in, double* out, cudaStream_t s);
 // y = a*x + b*y with a, b read from device scalars (nullable -> constants)

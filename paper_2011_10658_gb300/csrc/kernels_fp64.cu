@@ -5,6 +5,7 @@
 // replaces the hot contraction with tensor-core kernels.
 #include <cfloat>
 #include <atomic>
+#include <type_traits>
 #include <cstdio>
 
 #include "kernels.cuh"
@@ -265,6 +266,8 @@ __global__ void kc_reduce_kernel(const KOutput* __restrict__ outs, const int* __
 // ------------------------------------------------------------ reductions
 constexpr int RED_THREADS = 256;
 constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
+constexpr int LZ_BLOCKS = 1216;   // 8 x 152 SMs: the fused Lanczos passes keep GB300's FP64 pipes busy
+constexpr int kMaxLz = 129;       // basis vectors a fused pass handles
 
 __device__ __forceinline__ double block_sum(double v) {
   __shared__ double sh[RED_THREADS / 32];
@@ -338,6 +341,117 @@ __global__ void combine_kernel(const double* __restrict__ Q, long long ldq, int 
     double v = 0.0;
     for (int j = 0; j < k; ++j) v = fma(c[j], Q[(long long)j * ldq + i], v);
     x[i] = v;
+  }
+}
+
+// ---- fused Lanczos reorthogonalisation (one pass per Gram-Schmidt step)
+// Second classical Gram-Schmidt pass wanted (Daniel-Gragg-Kaufman-Stewart)?
+// The norm left after the first pass (*mid) against half the norm of the
+// three-term residual (c1[k] = w'.w').
+__device__ __forceinline__ bool lz_second_pass(const double* c1, int k, const double* mid, double ratio) {
+  return *mid < ratio * c1[k];
+}
+
+// With alpha != NULL (first pass): y <- w' = y - alpha v_a - beta v_b (the
+// three-term recurrence; v_b optional), written back.  Then
+// partial[col * gridDim.x + block] for col < k: V_col . w' over this block's
+// rows; col = k: w' . w'.  Columns in groups of eight per sweep over the
+// rows (each thread visits the same rows in every sweep, so it reads back
+// its own w').  With c1 != NULL the kernel runs only when a second pass is
+// wanted.
+// FF: products and sums in float-float arithmetic on the FP32 pipes (FP64
+// data; GB300's FP64 pipes would otherwise bound these passes).
+template <bool FF>
+__global__ void lz_dots_kernel(const double* __restrict__ V, long long ldq, int k, double* __restrict__ y,
+                               long long n, double* __restrict__ partial, const double* alpha,
+                               const double* __restrict__ va, const double* beta, const double* __restrict__ vb,
+                               const double* c1, const double* mid, double ratio) {
+  if (c1 && !lz_second_pass(c1, k, mid, ratio)) return;
+  __shared__ double sh[8][RED_THREADS / 32];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const double a = alpha ? *alpha : 0.0;
+  const double b = (alpha && vb) ? *beta : 0.0;
+  using A = typename std::conditional<FF, ff, double>::type;
+  for (int g0 = 0; g0 <= k; g0 += 8) {
+    A acc[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) acc[t] = A(0.f);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+      double yi = y[i];
+      if (alpha && g0 == 0) {
+        yi = fma(-a, va[i], yi);
+        if (vb) yi = fma(-b, vb[i], yi);
+        y[i] = yi;
+      }
+      const A ya = to_t<A>(yi);
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int col = g0 + t;
+        if (col < k) acc[t] = kc_fma(to_t<A>(V[(long long)col * ldq + i]), ya, acc[t]);
+        else if (col == k) acc[t] = kc_fma(ya, ya, acc[t]);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      double v = to_d<A>(acc[t]);
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (l == 0) sh[t][w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8 && g0 + (int)threadIdx.x <= k) {
+      double v = 0.0;
+      for (int u = 0; u < RED_THREADS / 32; ++u) v += sh[threadIdx.x][u];
+      partial[(long long)(g0 + threadIdx.x) * gridDim.x + blockIdx.x] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// out[col] = sum of partial[col * count ..] (col = blockIdx.x).  Same gate as
+// lz_dots_kernel.
+__global__ void lz_finish_kernel(const double* __restrict__ partial, int count, double* __restrict__ out,
+                                 const double* c1, int k1, const double* mid, double ratio) {
+  if (c1 && !lz_second_pass(c1, k1, mid, ratio)) return;
+  double v = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) v += partial[(long long)blockIdx.x * count + i];
+  v = block_sum(v);
+  if (threadIdx.x == 0) out[blockIdx.x] = v;
+}
+
+// y -= sum_{col < k} c[col] V_col, and partial[block] = this block's part of
+// |y|^2 afterwards.  Same gate as lz_dots_kernel.
+template <bool FF>
+__global__ void lz_axpy_norm_kernel(const double* __restrict__ V, long long ldq, int k, const double* __restrict__ c,
+                                    double* __restrict__ y, long long n, double* __restrict__ partial,
+                                    const double* c1, const double* mid, double ratio) {
+  if (c1 && !lz_second_pass(c1, k, mid, ratio)) return;
+  using A = typename std::conditional<FF, ff, double>::type;
+  __shared__ A cs[kMaxLz];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) cs[j] = to_t<A>(-c[j]);
+  __syncthreads();
+  A acc = A(0.f);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    A v = to_t<A>(y[i]);
+    for (int j = 0; j < k; ++j) v = kc_fma(cs[j], to_t<A>(V[(long long)j * ldq + i]), v);
+    y[i] = to_d<A>(v);
+    acc = kc_fma(v, v, acc);
+  }
+  const double r = block_sum(to_d<A>(acc));
+  if (threadIdx.x == 0) partial[blockIdx.x] = r;
+}
+
+// v = y / sqrt(nrm2), beta = sqrt(nrm2), *nrm_out = nrm2, with nrm2 the norm
+// after the second pass when it ran, else after the first.
+__global__ void lz_normalize_kernel(const double* __restrict__ y, double* __restrict__ v, long long n,
+                                    const double* c1, int k1, const double* mid, const double* nrm_second,
+                                    double ratio, double* beta, double* nrm_out) {
+  const double nrm2 = lz_second_pass(c1, k1, mid, ratio) ? *nrm_second : *mid;
+  const double inv = 1.0 / sqrt(nrm2);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    v[i] = y[i] * inv;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *beta = sqrt(fmax(nrm2, 0.0));
+    *nrm_out = nrm2;
   }
 }
 
@@ -924,6 +1038,35 @@ void launch_combine(const double* Q, long long ldq, int k, const double* c, doub
                     cudaStream_t s) {
   combine_kernel<<<grid_for(n), 256, 0, s>>>(Q, ldq, k, c, x, n);
   count_launches(1);
+}
+
+void launch_lz_reorth(const double* V, long long ldq, int k, double* y, long long n, double* partial, double* c1,
+                      double* c2, double* mid, double* nrm_second, double ratio, double* alpha_j,
+                      const double* beta_prev, double* beta_j, double* nrm_out, double* v_next, cudaStream_t s,
+                      int ff_arith) {
+  if (k < 1 || k >= kMaxLz) return;
+  auto dots = ff_arith ? lz_dots_kernel<true> : lz_dots_kernel<false>;
+  auto axpy = ff_arith ? lz_axpy_norm_kernel<true> : lz_axpy_norm_kernel<false>;
+  const double* vj = V + (long long)(k - 1) * ldq;
+  const double* vp = k >= 2 ? V + (long long)(k - 2) * ldq : nullptr;
+  // alpha_j = v_j . y
+  dot_partial_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(vj, y, n, partial);
+  finish_kernel<<<1, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, RED_BLOCKS, alpha_j);
+  // first pass on w' = y - alpha_j v_j - beta_{j-1} v_{j-1}: c1 = V^T w',
+  // c1[k] = w'.w'; y -= V c1; mid = |y|^2
+  dots<<<LZ_BLOCKS, RED_THREADS, 0, s>>>(V, ldq, k, y, n, partial, alpha_j, vj, beta_prev, vp, nullptr,
+                                                    nullptr, 0.0);
+  lz_finish_kernel<<<k + 1, RED_THREADS, 0, s>>>(partial, LZ_BLOCKS, c1, nullptr, 0, nullptr, 0.0);
+  axpy<<<LZ_BLOCKS, RED_THREADS, 0, s>>>(V, ldq, k, c1, y, n, partial, nullptr, nullptr, 0.0);
+  lz_finish_kernel<<<1, RED_THREADS, 0, s>>>(partial, LZ_BLOCKS, mid, nullptr, 0, nullptr, 0.0);
+  // second pass where the first removed more than the ratio allows
+  dots<<<LZ_BLOCKS, RED_THREADS, 0, s>>>(V, ldq, k, y, n, partial, nullptr, nullptr, nullptr, nullptr, c1,
+                                                    mid, ratio);
+  lz_finish_kernel<<<k, RED_THREADS, 0, s>>>(partial, LZ_BLOCKS, c2, c1, k, mid, ratio);
+  axpy<<<LZ_BLOCKS, RED_THREADS, 0, s>>>(V, ldq, k, c2, y, n, partial, c1, mid, ratio);
+  lz_finish_kernel<<<1, RED_THREADS, 0, s>>>(partial, LZ_BLOCKS, nrm_second, c1, k, mid, ratio);
+  lz_normalize_kernel<<<grid_for(n), 256, 0, s>>>(y, v_next, n, c1, k, mid, nrm_second, ratio, beta_j, nrm_out);
+  count_launches(11);
 }
 
 void launch_sqrt(const double* in, double* out, cudaStream_t s) {
