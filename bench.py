@@ -622,6 +622,55 @@ def run_heff_only(args):
     s.close()
 
 
+def run_profile_window(args):
+    """Profiling aid: the workload state; --warmup rounds of (centre to
+    bottom node 0, H_eff x at node 0, centre to its parent 32, H_eff x at
+    node 32), then one such round between cudaProfilerStart and
+    cudaProfilerStop (for ncu --profile-from-start off) after the centre is
+    back at node 0: the tensor-core bottom-node product, the QR and
+    digit-plane operator update of the bond above node 0, and the
+    tensor-core leg contractions of the upper-node product."""
+    import torch
+    import paper_2011_10658_gb300 as q
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    c = workloads.qed_couplings(G2)
+    s = q.TTN(q.Model(*L, Q=Q, **c), CHI, seed=SEED, precision=args.precision, stream=stream.cuda_stream)
+    gen = torch.Generator("cuda").manual_seed(0)
+    bufs = {}
+    for node in (0, 32):
+        n = s.node_size(node)
+        bufs[node] = (torch.randn(n, dtype=torch.float64, device="cuda", generator=gen),
+                      torch.empty(n, dtype=torch.float64, device="cuda"), n)
+
+    def one_round():
+        s.move_center(0)
+        x, y, n = bufs[0]
+        s.apply_heff_device(x.data_ptr(), y.data_ptr(), n)
+        s.move_center(32)
+        x, y, n = bufs[32]
+        s.apply_heff_device(x.data_ptr(), y.data_ptr(), n)
+
+    for _ in range(args.warmup):
+        one_round()
+    s.move_center(0)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.profiler.start()
+    ev0.record(stream)
+    x, y, n = bufs[0]
+    s.apply_heff_device(x.data_ptr(), y.data_ptr(), n)
+    s.move_center(32)
+    x, y, n = bufs[32]
+    s.apply_heff_device(x.data_ptr(), y.data_ptr(), n)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print(json.dumps({"mode": "profile", "ms_window": ev0.elapsed_time(ev1), "precision": args.precision,
+                      "sizes": {k: v[2] for k, v in bufs.items()}}), flush=True)
+    s.close()
+
+
 def batch_problems(n):
     """Independent problems of the batching workload (4x4x4, chi = 48): problem
     i has charge q = 2 (i mod 9), g^2 = (0.5, 2)[(i // 9) mod 2], m = (0.5, 1)[(i // 18)
@@ -675,6 +724,90 @@ def run_batch(args):
         "max_rel_dE_batch_vs_sequential": rel, "gpu_launches": launches}), flush=True)
 
 
+def run_scale(args):
+    """The scale configuration: 8x8x8 open lattice (512 dressed sites), t =
+    m = 1, g^2 in {0.5, 3}, charge excess Q = 32, chi = 128, seed 4, two
+    full sweeps from the seeded isometric start in the mixed precision.
+    One JSON line per g^2 with the sweep times, the H_eff x throughput and
+    the dominant class's roofline fraction, and the device memory the state
+    holds."""
+    import torch
+    import paper_2011_10658_gb300 as q
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    pk, src = measured_peaks()
+    peaks = {"bf16": pk["bf16_tflops_sustained"]}
+    if not args.no_probe:
+        peaks.update({k: v for k, v in probe_peaks("cuda").items() if k != "bf16"})
+    else:
+        peaks.update({"tf32": peaks["bf16"] * 1.1 / 2.25, "fp64": 1.25, "fp32_simt": 64.0})
+    for g2 in args.scale_g2:
+        torch.cuda.synchronize()
+        free0, total = torch.cuda.mem_get_info()
+        c = workloads.qed_couplings(g2)
+        model = q.Model(8, 8, 8, Q=32, **c)
+        t0 = time.time()
+        s = q.TTN(model, 128, seed=4, precision=args.precision, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        create_s = time.time() - t0
+        free1, _ = torch.cuda.mem_get_info()
+        s.set_profiling(True)
+        sampler = ClockSampler(0)
+        sampler.start()
+        l0 = q.launch_count()
+        sweeps = []
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = s.sweep(1, tol=TOL, max_krylov=KRYLOV, allow_noconv=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            st["ms"] = e0.elapsed_time(e1)
+            sweeps.append(st)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        elapsed_ms = ev0.elapsed_time(ev1)
+        launches = q.launch_count() - l0
+        clocks = sampler.stop()
+        free2, _ = torch.cuda.mem_get_info()
+        kt = {k: s.kernel_timing(k) for k in ALL_CLASSES}
+        flops = sum(kt[k]["flops_alg"] for k in PRODUCT_CLASSES)
+        classes = class_table(kt, elapsed_ms, peaks, args.precision)
+        dom = max(("tc_heff", "heff_simt_bottom", "heff_simt_upper", "move_ops", "move_ops_bottom"),
+                  key=lambda k: kt[k]["ms"])
+        d = kt[dom]
+        achieved = d["flops_alg"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
+        tp = "bf16" if args.precision == "bf16" else "tf32"
+        info = s.info()
+        e_tot, e_nopen, e_cls = s.energy()
+        line = {
+            "metric": "scale: TTN sweeps of the 8x8x8 chi=128 lattice (H_eff x TFLOP/s)",
+            "value": flops / (elapsed_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": 0, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "dtype": args.precision,
+            "data": "synthetic",
+            "config": {"workload": (f"8x8x8 open-boundary lattice QED (512 dressed sites), t=m=1, g2={g2:g}, Q=32, "
+                                    f"TTN chi=128 U(1) blocks, seed 4, {args.steps} sweeps from the seeded start, "
+                                    f"Lanczos tol {TOL:g}, Krylov {KRYLOV}, precision {args.precision}")},
+            "create_s": create_s,
+            "sweeps": [{k: v for k, v in st.items() if k != "seconds"} for st in sweeps],
+            "energy": e_tot, "energy_without_penalty": e_nopen, "class_energies": e_cls,
+            "n_nodes": info["n_nodes"], "max_node_size": info["max_node_size"],
+            "device_bytes": {"after_create": free0 - free1, "after_sweeps": free0 - free2, "gpu_total": total},
+            "roofline": {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": peaks[tp], "unit": "TFLOP/s",
+                         "frac": achieved / peaks[tp], "own_dtype_frac": classes.get(dom, {}).get("own_peak"),
+                         "share_of_step": d["ms"] / elapsed_ms},
+            "classes": classes, "peaks_tflops": peaks, "clocks": clocks, "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+        s.close()
+        del s, model
+        torch.cuda.synchronize()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -690,9 +823,12 @@ def main():
     ap.add_argument("--no-probe", action="store_true", help="skip the in-run GEMM peak probes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--mode", default="sweep", choices=["sweep", "heff", "batch"],
+    ap.add_argument("--mode", default="sweep", choices=["sweep", "heff", "batch", "scale", "profile"],
                     help="heff: only H_eff x products at --node (profiling aid); batch: batched "
-                         "independent problems against sequential sweeps")
+                         "independent problems against sequential sweeps; scale: the 8x8x8 chi=128 Q=32 "
+                         "lattice, --steps sweeps from the seeded start per g^2 of --scale-g2; profile: one "
+                         "bottom product, move and upper product inside a profiler window")
+    ap.add_argument("--scale-g2", type=float, nargs="+", default=[0.5, 3.0])
     ap.add_argument("--problems", type=int, default=8, help="batch mode: number of problems")
     ap.add_argument("--node", type=int, default=0)
     args = ap.parse_args()
@@ -704,6 +840,10 @@ def main():
         run_heff_only(args)
     elif args.mode == "batch":
         run_batch(args)
+    elif args.mode == "scale":
+        run_scale(args)
+    elif args.mode == "profile":
+        run_profile_window(args)
     else:
         run_native(args)
 

@@ -152,6 +152,77 @@ int ttn_sweep(ttn_state *s, int32_t n_sweeps, double tol, int32_t max_krylov, tt
  * vector with FP64 products until the FP64 residual reaches tol.  Default
  * mixed_tol: 1e-7 (TF32X3), 1e-5 (TF32), 1e-4 (BF16). */
 int ttn_set_mixed_tol(ttn_state *s, double mixed_tol);
+
+/* New couplings {t, m, ge2, cB, nu} (the order of the coupling classes) for
+ * the same lattice and charge sector.  Term coefficients become those a
+ * model created with these couplings has; every renormalized operator is
+ * rebuilt from the current tensors (no tensor changes) and the centre moves
+ * to the root.  A class whose coupling was zero at creation has no terms and
+ * cannot be switched on (QED_EINVAL); a class may be switched off (0).  Used
+ * by the driven optimisation below, which changes nu between sweeps. */
+int ttn_set_couplings(ttn_state *s, const double couplings[5]);
+
+/* Driven optimisation (Methods, "Numerical Convergence", the paragraph on
+ * the penalty of Eq. (16)) with the Lanczos tolerance raised each sweep
+ * (Methods, "Tensor Networks": the eigensolver's precision grows from
+ * sweep to sweep).  The penalty nu of sweep s:
+ *   linear stage:    nu_0 = nu_start, nu_{s+1} = nu_s + nu_step, until the
+ *                    energy <H + H_pen> after a sweep exceeds the previous
+ *                    sweep's by more than rise_rel |E_prev| (the "slight
+ *                    rise"; rise_rel keeps rounding from counting), which
+ *                    ends the stage;
+ *   quadratic stage: nu = nu_switch + quad_coef * nu_step * k^2 for the k-th
+ *                    sweep after the switch (k = 1, 2, ...; quad_coef < 1
+ *                    makes the first increments smaller than nu_step);
+ *   constant stage:  once a stage would pass nu_max, nu = nu_max for every
+ *                    later sweep; the run has converged when, after at least
+ *                    min_final_sweeps sweeps at nu_max, two consecutive
+ *                    energies differ by <= conv_rel |E|.
+ * The Lanczos tolerance of sweep s is max(tol_final, tol_start tol_factor^s).
+ * The paper gives no numbers for any of these: they are inputs. */
+typedef struct {
+  double nu_start, nu_step, quad_coef, nu_max;
+  double tol_start, tol_factor, tol_final;
+  double conv_rel, rise_rel;
+  int32_t min_final_sweeps; /* >= 2 */
+  int32_t max_sweeps;
+  int32_t max_krylov;
+} qed_drive;
+
+/* Schedule state: the stage (0 linear, 1 quadratic, 2 constant), the sweep
+ * index, nu and tolerance of the next sweep, done = 1 once converged. */
+typedef struct {
+  int32_t stage, sweep, since_switch, final_sweeps, done;
+  double nu, tol, nu_switch, e_prev;
+} qed_drive_state;
+
+/* Host-only schedule steps (no GPU): qed_drive_start sets nu and tol of
+ * sweep 0; qed_drive_next takes the energy of the sweep just run and sets
+ * those of the next one (or done).  QED_EINVAL on inconsistent settings
+ * (nu_start <= 0, nu_step <= 0, nu_max < nu_start, quad_coef <= 0, tolerances
+ * not positive, tol_factor outside (0, 1], conv_rel or rise_rel negative,
+ * min_final_sweeps < 2). */
+int qed_drive_start(const qed_drive *d, qed_drive_state *st);
+int qed_drive_next(const qed_drive *d, qed_drive_state *st, double energy);
+
+/* One record per sweep of ttn_drive. */
+typedef struct {
+  int32_t sweep, stage;
+  double nu, tol;
+  double energy;                 /* <H + H_pen> after the sweep */
+  double energy_without_penalty; /* <H> */
+  double delta_L;                /* sum over links |<L - 2>| (Methods, Numerical Convergence) */
+  int32_t matvecs, not_converged;
+  double max_rel_residual, seconds;
+} qed_drive_record;
+
+/* Run the driven optimisation on s from its current tensors: before each
+ * sweep ttn_set_couplings with the schedule's nu (the other couplings as
+ * the state has them), one sweep at the schedule's tolerance, then the
+ * energies and delta_L.  Records go to log[0 .. min(n, cap)) (caller-owned;
+ * NULL with cap 0 allowed); *n = sweeps run.  QED_OK once converged,
+ * QED_ENOCONV if max_sweeps ran out first (records valid). */
+int ttn_drive(ttn_state *s, const qed_drive *d, qed_drive_record *log, int32_t cap, int32_t *n);
 /* Bound of every mbarrier wait inside the tensor-core kernels of this state,
  * in polls (each poll is one mbarrier test plus a 32 ns sleep); polls < 0
  * restores the default (2^22 polls, about a quarter of a second).  A wait

@@ -341,6 +341,23 @@ class TTN:
         for nxt in self.path(self.center, target)[1:]:
             self.move(nxt)
 
+    def set_couplings(self, **couplings):
+        """New couplings (any of t, m, ge2, cB, nu) on the same lattice and
+        charge: the centre moves to the root, the term list is rebuilt for
+        the new couplings and every upward operator is recomputed from the
+        current tensors (downward ones follow the centre as it moves down
+        again, as after construction).  Used by the driven optimisation of
+        the penalty (Methods, "Numerical Convergence")."""
+        self.move_to(len(self.nodes) - 1)
+        self.p = _model.with_couplings(self.p, **couplings)
+        self.terms, self.const = _model.build_terms(self.p)
+        n = len(self.nodes)
+        self.up = [None] * n
+        self.down = [None] * n
+        for nd in self.nodes:
+            if nd.parent >= 0:
+                self.up[nd.index] = self._up_ops(nd.index)
+
     # ------------------------------------------------------------ sweep
     def optimize_node(self, idx, tol=1e-12):
         self.move_to(idx)

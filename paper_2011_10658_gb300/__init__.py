@@ -9,7 +9,7 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import QedError, QedParams, SweepStats, check, lib
+from ._lib import QedDrive, QedDriveRecord, QedDriveState, QedError, QedParams, SweepStats, check, lib
 
 PREC = {"fp64": 0, "tf32": 1, "bf16": 2, "tf32x3": 3}
 OP = {"I": 0, "M": 1, "MD": 2, "C": 3, "P": 4, "N": 5, "E2": 6, "PC": 8}
@@ -55,6 +55,32 @@ def batch_sweep(states, n=1, tol=1e-12, max_krylov=64, allow_noconv=False):
     return [dict(energy=st.energy, matvecs=st.matvecs, matvecs_mixed=st.matvecs_mixed,
                  node_updates=st.node_updates, not_converged=st.not_converged,
                  max_rel_residual=st.max_rel_residual, seconds=st.seconds) for st in stats]
+
+
+DRIVE_DEFAULTS = dict(nu_start=0.5, nu_step=0.5, quad_coef=0.25, nu_max=10.0, tol_start=1e-4, tol_factor=0.1,
+                      tol_final=1e-10, conv_rel=1e-8, rise_rel=1e-9, min_final_sweeps=2, max_sweeps=40,
+                      max_krylov=64)
+
+
+def drive_settings(**kw):
+    """qed_drive with DRIVE_DEFAULTS overridden by kw."""
+    unknown = set(kw) - set(DRIVE_DEFAULTS)
+    if unknown:
+        raise TypeError(f"unknown drive settings {sorted(unknown)}")
+    return QedDrive(**dict(DRIVE_DEFAULTS, **kw))
+
+
+def drive_start(d):
+    """qed_drive_start: schedule state of sweep 0."""
+    st = QedDriveState()
+    check(lib().qed_drive_start(ctypes.byref(d), ctypes.byref(st)))
+    return st
+
+
+def drive_next(d, st, energy):
+    """qed_drive_next: advance st past a sweep that ended at `energy`."""
+    check(lib().qed_drive_next(ctypes.byref(d), ctypes.byref(st), float(energy)))
+    return st
 
 
 class Model:
@@ -148,6 +174,22 @@ class TTN:
         check(lib().ttn_sweep(self._h, n, tol, max_krylov, ctypes.byref(st)), allow=(-4,) if allow_noconv else ())
         return dict(energy=st.energy, matvecs=st.matvecs, matvecs_mixed=st.matvecs_mixed, node_updates=st.node_updates,
                     not_converged=st.not_converged, max_rel_residual=st.max_rel_residual, seconds=st.seconds)
+
+    def set_couplings(self, t, m, ge2, cB, nu):
+        """ttn_set_couplings: new couplings, operators rebuilt, centre at the root."""
+        c = np.array([t, m, ge2, cB, nu], dtype=np.float64)
+        check(lib().ttn_set_couplings(self._h, _ptr(c, ctypes.c_double)))
+
+    def drive(self, allow_noconv=False, **settings):
+        """ttn_drive with drive_settings(**settings); (records, converged)."""
+        d = drive_settings(**settings)
+        cap = d.max_sweeps
+        log = (QedDriveRecord * cap)()
+        n = ctypes.c_int32()
+        rc = check(lib().ttn_drive(self._h, ctypes.byref(d), log, cap, ctypes.byref(n)),
+                   allow=(-4,) if allow_noconv else ())
+        recs = [{f: getattr(log[i], f) for f, _ in QedDriveRecord._fields_} for i in range(min(n.value, cap))]
+        return recs, rc == 0
 
     def optimize_node(self, node, tol=1e-12, max_krylov=64):
         e = ctypes.c_double()

@@ -33,6 +33,23 @@ class SweepStats(ctypes.Structure):
                 ("not_converged", c_int32), ("max_rel_residual", c_double), ("seconds", c_double)]
 
 
+class QedDrive(ctypes.Structure):
+    _fields_ = [("nu_start", c_double), ("nu_step", c_double), ("quad_coef", c_double), ("nu_max", c_double),
+                ("tol_start", c_double), ("tol_factor", c_double), ("tol_final", c_double), ("conv_rel", c_double),
+                ("rise_rel", c_double), ("min_final_sweeps", c_int32), ("max_sweeps", c_int32), ("max_krylov", c_int32)]
+
+
+class QedDriveState(ctypes.Structure):
+    _fields_ = [("stage", c_int32), ("sweep", c_int32), ("since_switch", c_int32), ("final_sweeps", c_int32),
+                ("done", c_int32), ("nu", c_double), ("tol", c_double), ("nu_switch", c_double), ("e_prev", c_double)]
+
+
+class QedDriveRecord(ctypes.Structure):
+    _fields_ = [("sweep", c_int32), ("stage", c_int32), ("nu", c_double), ("tol", c_double), ("energy", c_double),
+                ("energy_without_penalty", c_double), ("delta_L", c_double), ("matvecs", c_int32),
+                ("not_converged", c_int32), ("max_rel_residual", c_double), ("seconds", c_double)]
+
+
 # (name, restype, argtypes) for every entry point of include/qedttn.h
 SIGNATURES = [
     ("qed_last_error", ctypes.c_char_p, []),
@@ -75,6 +92,10 @@ SIGNATURES = [
     ("ttn_energy_grad", c_int, [c_void_p, c_int32, c_void_p, c_int64, c_double_p, c_void_p, c_double_p]),
     ("ttn_gradient_step", c_int, [c_void_p, c_double, c_double_p, c_double_p]),
     ("ttn_apply_heff_device_noalloc", c_int, [c_void_p, c_void_p, c_void_p, c_int64]),
+    ("ttn_set_couplings", c_int, [c_void_p, c_double_p]),
+    ("qed_drive_start", c_int, [ctypes.POINTER(QedDrive), ctypes.POINTER(QedDriveState)]),
+    ("qed_drive_next", c_int, [ctypes.POINTER(QedDrive), ctypes.POINTER(QedDriveState), c_double]),
+    ("ttn_drive", c_int, [c_void_p, ctypes.POINTER(QedDrive), ctypes.POINTER(QedDriveRecord), c_int32, c_int32_p]),
 ]
 
 STATUS = {0: "QED_OK", -1: "QED_EINVAL", -2: "QED_ENOMEM", -3: "QED_ECUDA", -4: "QED_ENOCONV",

@@ -1,4 +1,5 @@
 // C ABI of the qedttn library (see include/qedttn.h for the contract).
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -255,6 +256,130 @@ QED_API int ttn_set_mixed_tol(ttn_state* s, double mixed_tol) {
   if (!s) return fail(QED_EINVAL, "null state");
   if (!(mixed_tol > 0.0) || !(mixed_tol < 1.0)) return fail(QED_EINVAL, "mixed_tol must lie in (0, 1)");
   s->engine->mixed_tol = mixed_tol;
+  return QED_OK;
+}
+
+QED_API int ttn_set_couplings(ttn_state* s, const double couplings[5]) {
+  if (!s || !couplings) return fail(QED_EINVAL, "null argument");
+  QED_TRY(
+    qed::Engine* e = s->engine;
+    int rc = e->move_to(e->n_nodes() - 1);   // operators are rebuilt towards the root
+    if (rc) return engine_status(e, rc);
+    qed::Params np = e->params();
+    np.t = couplings[0]; np.m = couplings[1]; np.ge2 = couplings[2]; np.cB = couplings[3]; np.nu = couplings[4];
+    rc = e->set_couplings(np);
+    if (rc == -1) return fail(QED_EINVAL, e->error().c_str());
+    return engine_status(e, rc);)
+}
+
+namespace {
+
+int drive_check(const qed_drive* d) {
+  if (!d) return fail(QED_EINVAL, "null drive settings");
+  if (!(d->nu_start > 0.0) || !(d->nu_step > 0.0) || !(d->quad_coef > 0.0) || !(d->nu_max >= d->nu_start) ||
+      !std::isfinite(d->nu_max))
+    return fail(QED_EINVAL, "need 0 < nu_start <= nu_max (finite), nu_step > 0, quad_coef > 0");
+  if (!(d->tol_start > 0.0) || !(d->tol_final > 0.0) || !(d->tol_factor > 0.0) || !(d->tol_factor <= 1.0))
+    return fail(QED_EINVAL, "need tol_start > 0, tol_final > 0, 0 < tol_factor <= 1");
+  if (!(d->conv_rel >= 0.0) || !(d->rise_rel >= 0.0) || d->min_final_sweeps < 2 || d->max_sweeps < 1)
+    return fail(QED_EINVAL, "need conv_rel >= 0, rise_rel >= 0, min_final_sweeps >= 2, max_sweeps >= 1");
+  return QED_OK;
+}
+
+double drive_tol(const qed_drive* d, int sweep) {
+  return std::max(d->tol_final, d->tol_start * std::pow(d->tol_factor, (double)sweep));
+}
+
+}  // namespace
+
+QED_API int qed_drive_start(const qed_drive* d, qed_drive_state* st) {
+  if (int rc = drive_check(d)) return rc;
+  if (!st) return fail(QED_EINVAL, "null state");
+  std::memset(st, 0, sizeof(*st));
+  st->nu = d->nu_start;
+  if (st->nu >= d->nu_max) {
+    st->nu = d->nu_max;
+    st->stage = 2;
+  }
+  st->tol = drive_tol(d, 0);
+  return QED_OK;
+}
+
+QED_API int qed_drive_next(const qed_drive* d, qed_drive_state* st, double energy) {
+  if (int rc = drive_check(d)) return rc;
+  if (!st || !std::isfinite(energy)) return fail(QED_EINVAL, "null state or non-finite energy");
+  if (st->done) return QED_OK;
+  if (st->stage == 2) {
+    // the sweep just run was at nu_max
+    st->final_sweeps += 1;
+    if (st->final_sweeps >= d->min_final_sweeps && std::fabs(energy - st->e_prev) <= d->conv_rel * std::fabs(energy))
+      st->done = 1;
+  } else {
+    double next;
+    if (st->stage == 0 && st->sweep > 0 && energy - st->e_prev > d->rise_rel * std::fabs(st->e_prev)) {
+      // the energy rose: quadratic growth from the nu of this sweep
+      st->stage = 1;
+      st->nu_switch = st->nu;
+      st->since_switch = 1;
+      next = st->nu_switch + d->quad_coef * d->nu_step;
+    } else if (st->stage == 0) {
+      next = st->nu + d->nu_step;
+    } else {
+      st->since_switch += 1;
+      const double k = (double)st->since_switch;
+      next = st->nu_switch + d->quad_coef * d->nu_step * k * k;
+    }
+    if (next >= d->nu_max) {
+      next = d->nu_max;
+      st->stage = 2;
+    }
+    st->nu = next;
+  }
+  st->e_prev = energy;
+  st->sweep += 1;
+  st->tol = drive_tol(d, st->sweep);
+  return QED_OK;
+}
+
+QED_API int ttn_drive(ttn_state* s, const qed_drive* d, qed_drive_record* log, int32_t cap, int32_t* n) {
+  if (!s || !n || (cap > 0 && !log) || cap < 0) return fail(QED_EINVAL, "null argument or negative cap");
+  if (int rc = drive_check(d)) return rc;
+  if (d->max_krylov < 2 || d->max_krylov > 128) return fail(QED_EINVAL, "2 <= max_krylov <= 128");
+  *n = 0;
+  qed_drive_state st;
+  qed_drive_start(d, &st);
+  while (!st.done && st.sweep < d->max_sweeps) {
+    const qed::Params& p = s->engine->params();
+    if (p.nu != st.nu) {
+      const double c[5] = {p.t, p.m, p.ge2, p.cB, st.nu};
+      if (int rc = ttn_set_couplings(s, c)) return rc;
+    }
+    ttn_sweep_stats ss;
+    int rc = ttn_sweep(s, 1, st.tol, d->max_krylov, &ss);
+    if (rc != QED_OK && rc != QED_ENOCONV) return rc;
+    double et = 0.0, ew = 0.0;
+    if ((rc = ttn_energy(s, &et, &ew, nullptr))) return rc;
+    double sc[4];
+    int64_t ns = 0;
+    if ((rc = ttn_measure(s, QED_MEAS_SCALARS, sc, 4, &ns))) return rc;
+    if (*n < cap) {
+      qed_drive_record& r = log[*n];
+      r.sweep = st.sweep;
+      r.stage = st.stage;
+      r.nu = st.nu;
+      r.tol = st.tol;
+      r.energy = et;
+      r.energy_without_penalty = ew;
+      r.delta_L = sc[1];
+      r.matvecs = ss.matvecs;
+      r.not_converged = ss.not_converged;
+      r.max_rel_residual = ss.max_rel_residual;
+      r.seconds = ss.seconds;
+    }
+    *n += 1;
+    qed_drive_next(d, &st, et);
+  }
+  if (!st.done) return fail(QED_ENOCONV, "driven optimisation: max_sweeps reached before convergence");
   return QED_OK;
 }
 
@@ -618,7 +743,7 @@ QED_API int ttn_save(ttn_state* s, const char* path) {
     FILE* f = std::fopen(path, "wb");
     if (!f) return fail(QED_EINVAL, "cannot open the checkpoint file for writing");
     Fnv fnv;
-    const qed::Params& p = s->model->p;
+    const qed::Params& p = e->params();   // couplings as last set on the state
     const int32_t L[3] = {p.Lx, p.Ly, p.Lz};
     const double c[5] = {p.t, p.m, p.ge2, p.cB, p.nu};
     const int32_t chi = e->chi(), prec = e->precision(), nn = e->n_nodes();

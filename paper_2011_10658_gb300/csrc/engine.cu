@@ -17,6 +17,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <stdexcept>
+#include <set>
 
 namespace qed {
 
@@ -331,6 +332,26 @@ void* Engine::dalloc(size_t bytes) {
   bytes_ += (long long)bytes;
   track(p, bytes);
   return p;
+}
+
+void Engine::dfree_all(const std::vector<void*>& ptrs) {
+  std::set<void*> dead;
+  for (void* p : ptrs)
+    if (p) dead.insert(p);
+  if (dead.empty()) return;
+  cudaStreamSynchronize(stream_);
+  size_t w = 0;
+  for (size_t i = 0; i < allocs_.size(); ++i)
+    if (!dead.count(allocs_[i])) allocs_[w++] = allocs_[i];
+  allocs_.resize(w);
+  for (void* p : dead) {
+    auto r = ranges_.find((uintptr_t)p);
+    if (r != ranges_.end()) {
+      bytes_ -= (long long)r->second;
+      ranges_.erase(r);
+    }
+    cudaFree(p);
+  }
 }
 
 bool Engine::check(cudaError_t e, const char* what) {
@@ -1263,8 +1284,11 @@ int Engine::compute_up(int node) {
   for (int c = 0; c < N_CLASSES; ++c) cudaMemsetAsync(out.H[c], 0, dd * sizeof(double), stream_);
   for (auto& kv : out.term) cudaMemsetAsync(kv.second.ptr, 0, dd * sizeof(double), stream_);
   int rc = 0;
-  if (bottom && precision_ != PREC_FP64) {
+  int max_sector = 0;
+  for (int d : L.leg[2].dim) max_sector = std::max(max_sector, d);
+  if (bottom && precision_ != PREC_FP64 && max_sector <= 64) {
     // mixed states: FP64-accurate digit-plane products on the tensor cores
+    // (output sectors up to 64 wide; wider ones take the FP64 kernel below)
     std::vector<std::pair<double*, double>> oc_terms;
     std::vector<int> oc_keys;
     for (const Contrib& c : cs) {
@@ -1431,6 +1455,7 @@ int Engine::compute_up_oz(int node, const std::vector<std::pair<double*, double>
             }
             if (!nnz) continue;
             int* dm = (int*)dalloc((size_t)rows * sizeof(int));
+            op.owned.push_back(dm);
             cudaMemcpyAsync(dm, m.data(), (size_t)rows * sizeof(int), cudaMemcpyHostToDevice, stream_);
             js.push_back({dm, oc, oc, out.H[cl], v, nnz});
           }
@@ -2957,6 +2982,75 @@ int Engine::load_tensors(const double* const* host, const long long* sizes, int 
     }
   center_ = (int)nodes_.size() - 1;
   return check(cudaGetLastError(), "load") ? 0 : -3;
+}
+
+int Engine::set_couplings(const Params& np) {
+  if (np.Lx != p_.Lx || np.Ly != p_.Ly || np.Lz != p_.Lz || np.boundary != p_.boundary || np.Q != p_.Q) {
+    err_ = "set_couplings: the lattice, the boundary and the charge sector are fixed";
+    return -1;
+  }
+  const double oldc[N_CLASSES] = {p_.t, p_.m, p_.ge2, p_.cB, p_.nu};
+  const double newc[N_CLASSES] = {np.t, np.m, np.ge2, np.cB, np.nu};
+  for (int c = 0; c < N_CLASSES; ++c)
+    if (!std::isfinite(newc[c]) || (oldc[c] == 0.0 && newc[c] != 0.0)) {
+      err_ = "set_couplings: a coupling is not finite, or its class was zero at creation (no terms)";
+      return -1;
+    }
+  // same term list as a fresh model with these couplings; a class switched
+  // off keeps its terms with coefficient zero
+  Params sub = np;
+  double* subc[N_CLASSES] = {&sub.t, &sub.m, &sub.ge2, &sub.cB, &sub.nu};
+  for (int c = 0; c < N_CLASSES; ++c)
+    if (newc[c] == 0.0) *subc[c] = 1.0;
+  std::vector<Term> nt;
+  double cst = 0.0;
+  build_terms(sub, &nt, &cst);
+  if (nt.size() != terms_.size()) {
+    err_ = "set_couplings: term list changed";
+    return -1;
+  }
+  for (size_t i = 0; i < nt.size(); ++i)
+    if (nt[i].cls != terms_[i].cls || nt[i].ops.size() != terms_[i].ops.size()) {
+      err_ = "set_couplings: term list changed";
+      return -1;
+    }
+  for (size_t i = 0; i < nt.size(); ++i) terms_[i].coef = newc[nt[i].cls] == 0.0 ? 0.0 : nt[i].coef;
+  constant_ = cst;
+  p_.t = np.t; p_.m = np.m; p_.ge2 = np.ge2; p_.cB = np.cB; p_.nu = np.nu;
+  // drop everything that holds a coefficient
+  clear_plan_caches();
+  clear_tc_cache();
+  tg_cache_.clear();
+  std::vector<void*> dead;
+  for (auto& kv : oz_cache_)
+    for (void* p : kv.second->owned) dead.push_back(p);
+  oz_cache_.clear();
+  for (auto it = rowmaps_.begin(); it != rowmaps_.end();) {
+    if (it->first.second <= -1000) {   // site Hamiltonian maps (coefficients in their values)
+      for (RowMap& rm : it->second) {
+        dead.push_back(rm.map);
+        dead.push_back(rm.val);
+      }
+      it = rowmaps_.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  for (auto& kv : inv_maps_) {
+    dead.push_back(kv.second.map);
+    dead.push_back(kv.second.val);
+  }
+  inv_maps_.clear();
+  dfree_all(dead);
+  ++gen_;
+  tc_w_node_ = -1;
+  for (const TreeNode& nd : nodes_)
+    if (nd.parent >= 0) {
+      int rc = compute_up(nd.index);
+      if (rc) return rc;
+    }
+  center_ = (int)nodes_.size() - 1;
+  return check(cudaGetLastError(), "set_couplings") ? 0 : -3;
 }
 
 int Engine::noalloc_worklist(const double* x, double* y, KTile* tiles, int max_tiles, KOutput* outs, int max_outs,

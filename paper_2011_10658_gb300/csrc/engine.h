@@ -200,6 +200,7 @@ struct OzPlan {
   long long partial_elems = 0;
   int npad = 32;
   double flops = 0.0;   // algorithmic: 2 x mapped rows x chi_out x chi_in per job
+  std::vector<void*> owned;   // row selections of the site Hamiltonians (engine allocations)
   void release();
   ~OzPlan() { release(); }
 };
@@ -248,6 +249,14 @@ class Engine {
   // Replace every tensor (tree isometric towards the root, root normalised)
   // and rebuild all renormalized operators; the centre becomes the root.
   int load_tensors(const double* const* host, const long long* sizes, int n);
+  // New coupling constants (t, m, ge2, cB, nu) on the same lattice and
+  // charge sector: the term coefficients are replaced (the same expressions
+  // as at creation), every cached plan or row map that holds a coefficient
+  // is dropped and freed, and all renormalized operators are rebuilt from
+  // the current tensors; the centre becomes the root.  A coupling class that
+  // was zero at creation has no terms and cannot be switched on (-1).
+  int set_couplings(const Params& np);
+  const Params& params() const { return p_; }
   int move_to(int target);
   // Work list of y = H_eff x at a bottom-node centre for the FP64 grouped
   // GEMM, written into caller-provided arrays with no allocation: x and y
@@ -447,6 +456,8 @@ class Engine {
   bool in_own_range(const void* p, long long lo_off, long long hi_off) const;
   std::vector<const Engine*> peers_;   // other engines whose allocations a grouped plan may touch
   void* dalloc(size_t bytes);
+  // free allocations made by dalloc (null entries ignored)
+  void dfree_all(const std::vector<void*>& ptrs);
   bool check(cudaError_t e, const char* what);
   const SiteOp* site_op(int parity, const OpKey& key);
   bool touches(int term, int node) const;

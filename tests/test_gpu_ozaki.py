@@ -29,7 +29,11 @@ def q():
     return pkg
 
 
-@pytest.mark.parametrize("L,chi,seed,path", [((2, 2, 2), 8, 0, (0, 4, 1, 5)), ((4, 4, 4), 64, 1, (0, 32, 1, 32, 17))])
+# chi = 96 on 2x2x2: bottom-bond sectors up to 55 wide (64-column tiles);
+# chi = 128: a 74-wide sector, which the FP64 kernel takes instead
+@pytest.mark.parametrize("L,chi,seed,path", [((2, 2, 2), 8, 0, (0, 4, 1, 5)), ((2, 2, 2), 96, 0, (0, 4, 1, 5)),
+                                             ((2, 2, 2), 128, 0, (0, 4, 1, 5)),
+                                             ((4, 4, 4), 64, 1, (0, 32, 1, 32, 17))])
 def test_bottom_operator_update_matches_fp64(q, L, chi, seed, path):
     c = workloads.qed_couplings(1.0)
     a = q.TTN(q.Model(*L, Q=0, **c), chi, seed=seed, precision="fp64")
