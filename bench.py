@@ -671,6 +671,104 @@ def run_profile_window(args):
     s.close()
 
 
+def _links(L, periodic):
+    """(x, mu) of every link in the library's order (sites, then mu)."""
+    Lx, Ly, Lz = L
+    dims = (Lx, Ly, Lz)
+    out = []
+    for s in range(Lx * Ly * Lz):
+        c = [s % Lx, (s // Lx) % Ly, s // (Lx * Ly)]
+        for mu in range(3):
+            d = list(c)
+            d[mu] += 1
+            if periodic and dims[mu] > 1:
+                d[mu] %= dims[mu]
+            if d[mu] < dims[mu]:
+                out.append((s, mu))
+    return out
+
+
+def run_physics(args):
+    """The paper's physics workloads on the same engine (driven penalty,
+    then the observables), one JSON line each:
+      finite density: 4x4x4 open, Q = 16, g2 = 1: sigma(l) by surface layer
+        (Results, "Finite density");
+      zero charge, periodic: 4x4x4, Q = 0, g2 = 2 (ge2/2 = t = 1), cB = 0
+        and cB = 1/(2 g2), m in {-1, 0.5, 2}: rho (Results, "Transition at
+        zero charge");
+      quantum capacitor: 4x4x4 open, Q = 0, chemical potentials -/+ mu0 on
+        the faces x = 0 and x = 3, m in {-1, 1}: q_c(d) and E_c(d) along x
+        (Results, "Quantum capacitor").
+    Bond dimension --physics-chi (default 32), seed 7; the driven schedule
+    of the library with nu_max = 10 max(|t|, |m|, ge2/2, cB)."""
+    import numpy as np
+    import torch
+    import paper_2011_10658_gb300 as q
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    chi = args.physics_chi
+    L4 = (4, 4, 4)
+    N = 64
+
+    def drive(model, nu_max):
+        s = q.TTN(model, chi, seed=7, precision=args.precision, stream=stream.cuda_stream)
+        t0 = time.time()
+        recs, conv = s.drive(allow_noconv=True, nu_start=0.5, nu_step=2.0, quad_coef=0.25, nu_max=nu_max,
+                             tol_start=1e-4, tol_factor=0.3, tol_final=1e-8, conv_rel=1e-7, rise_rel=1e-9,
+                             min_final_sweeps=2, max_sweeps=args.physics_sweeps, max_krylov=KRYLOV)
+        torch.cuda.synchronize()
+        return s, recs, conv, time.time() - t0
+
+    def base_line(name, recs, conv, secs, extra):
+        last = recs[-1]
+        line = {"mode": "physics", "workload": name, "chi": chi, "precision": args.precision, "seed": 7,
+                "sweeps": len(recs), "converged": conv, "seconds": secs, "energy": last["energy"],
+                "energy_without_penalty": last["energy_without_penalty"], "delta_L": last["delta_L"],
+                "nu_schedule": [r["nu"] for r in recs], "stages": [r["stage"] for r in recs],
+                "delta_L_per_sweep": [r["delta_L"] for r in recs],
+                "energy_per_sweep": [r["energy"] for r in recs]}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+
+    # finite density
+    c = workloads.qed_couplings(1.0)
+    nu_max = c["nu"]
+    s, recs, conv, secs = drive(q.Model(*L4, Q=16, **dict(c, nu=0.5)), nu_max)
+    sc = s.measure("scalars")
+    base_line("finite density 4x4x4 open Q=16 g2=1", recs, conv, secs,
+              {"sigma_l": [float(v) for v in s.measure("sigma")], "rho": float(sc[0]), "total_charge": float(sc[2])})
+    s.close()
+
+    # zero charge, periodic
+    for cb_on in (False, True):
+        for mass in (-1.0, 0.5, 2.0):
+            c = dict(t=1.0, m=mass, ge2=2.0, cB=(0.25 if cb_on else 0.0), nu=0.5)
+            nu_max = 10.0 * max(1.0, abs(mass), 1.0, c["cB"])
+            s, recs, conv, secs = drive(q.Model(*L4, Q=0, boundary=1, **c), nu_max)
+            sc = s.measure("scalars")
+            base_line(f"zero charge 4x4x4 periodic g2=2 cB={c['cB']:g} m={mass:g}", recs, conv, secs,
+                      {"rho": float(sc[0]), "total_charge": float(sc[2])})
+            s.close()
+
+    # quantum capacitor
+    mu0 = args.capacitor_mu
+    mu = [(-mu0 if s_ % 4 == 0 else (mu0 if s_ % 4 == 3 else 0.0)) for s_ in range(N)]
+    parity = np.array([1 if (s_ % 4 + (s_ // 4) % 4 + s_ // 16) % 2 == 0 else -1 for s_ in range(N)])
+    links = _links(L4, False)
+    for mass in (-1.0, 1.0):
+        c = dict(t=1.0, m=mass, ge2=2.0, cB=0.25, nu=0.5)
+        nu_max = 10.0 * max(1.0, abs(mass), 1.0)
+        s, recs, conv, secs = drive(q.Model(*L4, Q=0, mu=mu, **c), nu_max)
+        phi = np.array(s.measure("phi"))
+        el = np.array(s.measure("elink"))
+        qc = [float(2.0 / 16 * sum(parity[x] * phi[x] for x in range(N) if x % 4 == d)) for d in range(4)]
+        ec = [float(2.0 / 16 * sum(el[i] for i, (x, mu_) in enumerate(links) if mu_ == 0 and x % 4 == d))
+              for d in range(3)]
+        base_line(f"capacitor 4x4x4 open plates mu=-/+{mu0:g} on x=0/3, g2=2 cB=0.25 m={mass:g}", recs, conv,
+                  secs, {"q_c": qc, "E_c": ec, "rho": float(s.measure("scalars")[0])})
+        s.close()
+
+
 def batch_problems(n):
     """Independent problems of the batching workload (4x4x4, chi = 48): problem
     i has charge q = 2 (i mod 9), g^2 = (0.5, 2)[(i // 9) mod 2], m = (0.5, 1)[(i // 18)
@@ -823,11 +921,15 @@ def main():
     ap.add_argument("--no-probe", action="store_true", help="skip the in-run GEMM peak probes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--mode", default="sweep", choices=["sweep", "heff", "batch", "scale", "profile"],
+    ap.add_argument("--mode", default="sweep", choices=["sweep", "heff", "batch", "scale", "profile", "physics"],
                     help="heff: only H_eff x products at --node (profiling aid); batch: batched "
                          "independent problems against sequential sweeps; scale: the 8x8x8 chi=128 Q=32 "
                          "lattice, --steps sweeps from the seeded start per g^2 of --scale-g2; profile: one "
-                         "bottom product, move and upper product inside a profiler window")
+                         "bottom product, move and upper product inside a profiler window; physics: the "
+                         "finite-density, periodic zero-charge and capacitor workloads (driven sweeps)")
+    ap.add_argument("--physics-chi", type=int, default=32)
+    ap.add_argument("--physics-sweeps", type=int, default=14)
+    ap.add_argument("--capacitor-mu", type=float, default=4.0)
     ap.add_argument("--scale-g2", type=float, nargs="+", default=[0.5, 3.0])
     ap.add_argument("--problems", type=int, default=8, help="batch mode: number of problems")
     ap.add_argument("--node", type=int, default=0)
@@ -844,6 +946,8 @@ def main():
         run_scale(args)
     elif args.mode == "profile":
         run_profile_window(args)
+    elif args.mode == "physics":
+        run_physics(args)
     else:
         run_native(args)
 

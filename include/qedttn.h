@@ -39,7 +39,11 @@ extern "C" {
  * penalty of Eq. (16).  Q is the total charge sum_x (psi^dag psi -
  * (1 - (-1)^x)/2) (Eq. (1) text).  boundary: 0 = open, every site keeps its
  * six half-links and the ones pointing out of the lattice are free
- * ("dangling", each costing ge2/2 (1 - k)^2); other values are rejected. */
+ * ("dangling", each costing ge2/2 (1 - k)^2); 1 = periodic (Results,
+ * "Transition at zero charge"): every direction with more than one site
+ * wraps around, so its half-links all belong to links (on an extent of 2
+ * two links join the same pair of sites), while a direction of extent 1
+ * keeps open, dangling half-links.  Other values are rejected. */
 typedef struct {
   int32_t Lx, Ly, Lz;
   int32_t boundary;
@@ -100,11 +104,19 @@ int qed_local_op(int parity, int op_kind, int j1, int j2, int16_t *src, double *
  * must be powers of two with at least two sites. */
 int qed_model_create(const qed_params *p, qed_model **out);
 void qed_model_destroy(qed_model *m);
+/* Local chemical potentials (Methods, "Fermionic compact representation":
+ * the diagonal local terms used to pin charges; Results, "Quantum
+ * capacitor": large potentials on two opposite faces): one term
+ * mu[x] psi^dag_x psi_x per site with mu[x] != 0, in a coupling class of
+ * its own (class 5).  n = number of sites (caller-owned mu, copied), or
+ * n = 0 to remove them.  Applies to states created from the model
+ * afterwards.  QED_ENAN on a non-finite entry. */
+int qed_model_set_site_potential(qed_model *m, const double *mu, int32_t n);
 /* n_sites, number of product terms, number of tree nodes, additive constant
  * (zero: the penalty of Eq. (16) is written as nu sum_k P^k_x (1 -
  * P^{2-k}_y) per link, an exact rewrite of nu (1 - delta_{2,L})). */
 int qed_model_info(const qed_model *m, int32_t *n_sites, int32_t *n_terms, int32_t *n_nodes, double *constant);
-/* Term list: for term i, coef[i], cls[i] (0 t, 1 m, 2 ge2, 3 cB, 4 nu) and up
+/* Term list: for term i, coef[i], cls[i] (0 t, 1 m, 2 ge2, 3 cB, 4 nu, 5 mu) and up
  * to four factors ops[i][f] = (site, kind, a, b) with n_ops[i] factors. */
 int qed_model_terms(const qed_model *m, double *coef, int32_t *cls, int32_t *n_ops, int32_t *ops /* [n][4][4] */,
                     int64_t cap, int64_t *n);
@@ -287,7 +299,8 @@ int ttn_node_size(ttn_state *s, int32_t node, int64_t *n);
 
 /* <H + H_pen> of the state (constant included) and the same without the
  * penalty; E_class[5] (nullable) = <H_class> per coupling class t, m, ge2,
- * cB, nu (constant in the nu class), i.e. dE/dc_class times c_class. */
+ * cB, nu (constant in the nu class), i.e. dE/dc_class times c_class.  The
+ * chemical-potential energy (class 5) is E_total minus the sum of these. */
 int ttn_energy(ttn_state *s, double *E_total, double *E_without_penalty, double *E_class);
 
 /* Observables (Results text and Eq. (16a), (17b)), centre moved to the root:

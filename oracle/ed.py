@@ -34,7 +34,7 @@ from . import model as _model
 def dressed_hamiltonian(p):
     """Sparse H on the full dressed space of a lattice with N sites
     (267^N states; use N <= 2).  Returns (H, charge vector, constant)."""
-    lat = _model.Lattice(p.Lx, p.Ly, p.Lz)
+    lat = _model.lattice(p)
     n = lat.n_sites
     if n > 2:
         raise ValueError("dressed ED is limited to two sites")
@@ -70,7 +70,7 @@ def dressed_ed(p, k=1):
 
 def _config_blocks(p):
     """Enumerate Gauss-law configurations (phi, E) grouped by dangling flux F."""
-    lat = _model.Lattice(p.Lx, p.Ly, p.Lz)
+    lat = _model.lattice(p)
     n = lat.n_sites
     links = lat.links()
     ndang = [len(lat.dangling(s)) for s in range(n)]
@@ -173,7 +173,7 @@ def dressed_ed_fixed_dangling(p, dangling_k, k=1):
     to its fixed occupation k.  Dangling occupations are conserved by every
     term, so this block is an exact invariant subspace.  Feasible for a few
     sites (each site keeps only its rows matching ``dangling_k[s]``)."""
-    lat = _model.Lattice(p.Lx, p.Ly, p.Lz)
+    lat = _model.lattice(p)
     n = lat.n_sites
     keep = []
     for s in range(n):

@@ -16,7 +16,13 @@ Readings of the paper used here (the library takes the same ones):
   read on the lower site, Eq. (10);
 * the penalty of Eq. (16), nu * (1 - delta_{2,L}) per internal link, is
   written as nu * sum_k P^k_{x,+mu} (x) (1 - P^{2-k}_{x+mu,-mu}) (exact,
-  since sum_k P^k = 1), so no additive constant remains.
+  since sum_k P^k = 1), so no additive constant remains;
+* periodic boundaries (Results, "Transition at zero charge"): every
+  direction with more than one site wraps around (an extent of 2 gives two
+  links between the same two sites); a direction of extent 1 stays open;
+* local chemical potentials (Methods: diagonal local terms that pin
+  charges; Results, "Quantum capacitor"): mu_x psi^dag_x psi_x per site, a
+  class of its own ('mu').
 """
 from dataclasses import dataclass, field, replace
 
@@ -42,6 +48,8 @@ class Params:
     cB: float = 0.5
     nu: float = 10.0
     Q: int = 0
+    boundary: int = 0          # 0 open, 1 periodic
+    mu: tuple = ()             # chemical potential per site (empty: none)
 
 
 @dataclass(frozen=True)
@@ -60,6 +68,7 @@ class Lattice:
     Lx: int
     Ly: int
     Lz: int
+    periodic: bool = False
 
     @property
     def n_sites(self):
@@ -87,6 +96,8 @@ class Lattice:
     def neighbour(self, s, mu, step=1):
         c = list(self.coords(s))
         c[mu] += step
+        if self.periodic and self.dims()[mu] > 1:
+            c[mu] %= self.dims()[mu]
         return self.index(*c) if self.inside(c) else None
 
     def links(self):
@@ -133,12 +144,17 @@ class Lattice:
         return tuple(sorted(mask))
 
 
+def lattice(p: Params):
+    """The lattice of p (open or periodic)."""
+    return Lattice(p.Lx, p.Ly, p.Lz, periodic=(p.boundary == 1))
+
+
 def build_terms(p: Params):
     """Product terms of Eq. (1) + Eq. (16) and the constant nu * N_links.
 
     Returns (terms, constant).  Site ops are keys understood by
     ``oracle.fock.site_op``."""
-    lat = Lattice(p.Lx, p.Ly, p.Lz)
+    lat = lattice(p)
     terms = []
     # staggered mass m sum_x (-1)^x psi^dag psi  (Eq. (1), second line)
     for s in range(lat.n_sites):
@@ -171,6 +187,9 @@ def build_terms(p: Params):
     for (x, mu, y) in links:
         for k in range(3):
             terms.append(Term(p.nu, "nu", 1.0, ((x, ("P", plus(mu), k)), (y, ("PC", minus(mu), 2 - k)))))
+    # local chemical potentials mu_x psi^dag_x psi_x
+    for s, mu_s in enumerate(p.mu):
+        terms.append(Term(float(mu_s), "mu", 1.0, ((s, ("n",)),)))
     constant = 0.0
     # drop exactly-zero couplings: they contribute nothing
     terms = [tm for tm in terms if tm.coef != 0.0]
@@ -183,6 +202,6 @@ def with_couplings(p: Params, **kw):
 
 def class_only(p: Params, cls):
     """Params keeping only the coupling ``cls`` (others set to zero)."""
-    zero = dict(t=0.0, m=0.0, ge2=0.0, cB=0.0, nu=0.0)
+    zero = dict(t=0.0, m=0.0, ge2=0.0, cB=0.0, nu=0.0, mu=())
     zero[cls] = getattr(p, cls)
     return replace(p, **zero)

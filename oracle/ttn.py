@@ -73,7 +73,7 @@ class TTN:
     def __init__(self, p: _model.Params, chi, seed, build_ops=True):
         self.p = p
         self.chi = chi
-        self.lat = _model.Lattice(p.Lx, p.Ly, p.Lz)
+        self.lat = _model.lattice(p)
         self.nodes = _tree.build_tree(p.Lx, p.Ly, p.Lz)
         self.bonds = _tree.sector_table(p, chi, self.nodes)
         self.terms, self.const = _model.build_terms(p)

@@ -14,7 +14,7 @@ from ._lib import QedDrive, QedDriveRecord, QedDriveState, QedError, QedParams, 
 PREC = {"fp64": 0, "tf32": 1, "bf16": 2, "tf32x3": 3}
 OP = {"I": 0, "M": 1, "MD": 2, "C": 3, "P": 4, "N": 5, "E2": 6, "PC": 8}
 MEAS = {"probs": 0, "phi": 1, "nx": 2, "qx": 3, "k": 4, "elink": 5, "scalars": 6, "sigma": 7}
-CLASSES = ("t", "m", "ge2", "cB", "nu")
+CLASSES = ("t", "m", "ge2", "cB", "nu")   # scalar couplings; terms of class 5 are the chemical potentials
 
 
 def _ptr(a, ctype):
@@ -86,11 +86,19 @@ def drive_next(d, st, energy):
 class Model:
     """Lattice, term list and tree (qed_model_create)."""
 
-    def __init__(self, Lx, Ly, Lz, t=1.0, m=1.0, ge2=1.0, cB=0.5, nu=10.0, Q=0, boundary=0):
+    def __init__(self, Lx, Ly, Lz, t=1.0, m=1.0, ge2=1.0, cB=0.5, nu=10.0, Q=0, boundary=0, mu=None):
+        """boundary: 0 open, 1 periodic; mu: chemical potential per site
+        (qed_model_set_site_potential), None for none."""
         self.params = QedParams(Lx, Ly, Lz, boundary, t, m, ge2, cB, nu, Q)
         h = ctypes.c_void_p()
         check(lib().qed_model_create(ctypes.byref(self.params), ctypes.byref(h)))
         self._h = h
+        if mu is not None:
+            self.set_site_potential(mu)
+
+    def set_site_potential(self, mu):
+        mu = np.ascontiguousarray(mu, dtype=np.float64)
+        check(lib().qed_model_set_site_potential(self._h, _ptr(mu, ctypes.c_double), mu.size))
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -93,6 +93,7 @@ SIGNATURES = [
     ("ttn_gradient_step", c_int, [c_void_p, c_double, c_double_p, c_double_p]),
     ("ttn_apply_heff_device_noalloc", c_int, [c_void_p, c_void_p, c_void_p, c_int64]),
     ("ttn_set_couplings", c_int, [c_void_p, c_double_p]),
+    ("qed_model_set_site_potential", c_int, [c_void_p, c_double_p, c_int32]),
     ("qed_drive_start", c_int, [ctypes.POINTER(QedDrive), ctypes.POINTER(QedDriveState)]),
     ("qed_drive_next", c_int, [ctypes.POINTER(QedDrive), ctypes.POINTER(QedDriveState), c_double]),
     ("ttn_drive", c_int, [c_void_p, ctypes.POINTER(QedDrive), ctypes.POINTER(QedDriveRecord), c_int32, c_int32_p]),

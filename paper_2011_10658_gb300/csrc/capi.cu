@@ -91,7 +91,7 @@ QED_API int qed_local_op(int parity, int op_kind, int j1, int j2, int16_t* src, 
 QED_API int qed_model_create(const qed_params* p, qed_model** out) {
   if (!p || !out) return fail(QED_EINVAL, "null argument");
   *out = nullptr;
-  if (p->boundary != 0) return fail(QED_EUNSUPPORTED, "only open boundaries (boundary = 0) are built");
+  if (p->boundary != 0 && p->boundary != 1) return fail(QED_EINVAL, "boundary must be 0 (open) or 1 (periodic)");
   if (!pow2(p->Lx) || !pow2(p->Ly) || !pow2(p->Lz) || p->Lx * p->Ly * p->Lz < 2 || p->Lx * p->Ly * p->Lz > 4096)
     return fail(QED_EINVAL, "lattice extents must be powers of two, 2 <= sites <= 4096");
   const double c[5] = {p->t, p->m, p->ge2, p->cB, p->nu};
@@ -108,6 +108,18 @@ QED_API int qed_model_create(const qed_params* p, qed_model** out) {
 }
 
 QED_API void qed_model_destroy(qed_model* m) { delete m; }
+
+QED_API int qed_model_set_site_potential(qed_model* m, const double* mu, int32_t n) {
+  if (!m) return fail(QED_EINVAL, "null model");
+  const int N = m->p.Lx * m->p.Ly * m->p.Lz;
+  if (n != 0 && (n != N || !mu)) return fail(QED_EINVAL, "need one chemical potential per site (or n = 0)");
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(mu[i])) return fail(QED_ENAN, "non-finite chemical potential");
+  QED_TRY(
+    m->p.mu.assign(mu, mu + n);
+    qed::build_terms(m->p, &m->terms, &m->constant);
+    return QED_OK;)
+}
 
 QED_API int qed_model_info(const qed_model* m, int32_t* n_sites, int32_t* n_terms, int32_t* n_nodes, double* constant) {
   if (!m) return fail(QED_EINVAL, "null model");
@@ -524,14 +536,14 @@ QED_API int ttn_energy(ttn_state* s, double* E_total, double* E_without_penalty,
     if (E_total) *E_total = tot;
     if (E_without_penalty) *E_without_penalty = tot - parts[qed::CLS_NU];
     if (E_class)
-      for (int c = 0; c < qed::N_CLASSES; ++c) E_class[c] = parts[c];
+      for (int c = 0; c < qed::N_COUPLINGS; ++c) E_class[c] = parts[c];
     return QED_OK;)
 }
 
 QED_API int ttn_measure(ttn_state* s, int kind, double* out, int64_t cap, int64_t* n) {
   if (!s) return fail(QED_EINVAL, "null state");
   const qed::Params& p = s->model->p;
-  qed::Lattice lat{p.Lx, p.Ly, p.Lz};
+  qed::Lattice lat{p.Lx, p.Ly, p.Lz, p.boundary == 1};
   const int N = lat.n_sites();
   int64_t need = 0;
   int layers = 0;
@@ -794,7 +806,7 @@ QED_API int ttn_load(const qed_model* m, const char* path, void* cuda_stream, tt
       std::vector<qed::Sectors> bonds;
       std::string err;
       if (!qed::sector_table(p, h.chi, m->nodes, &bonds, &err)) { std::fclose(f); return fail(QED_EINVAL, err.c_str()); }
-      qed::Lattice lat{p.Lx, p.Ly, p.Lz};
+      qed::Lattice lat{p.Lx, p.Ly, p.Lz, p.boundary == 1};
       for (const qed::TreeNode& nd : m->nodes) {
         qed::Sectors legs[2];
         for (int c = 0; c < 2; ++c)
@@ -854,7 +866,9 @@ QED_API int ttn_energy_grad(ttn_state* s, int32_t node, const double* psi_device
     if (dE_dpsi_device && n != s->engine->node_size(s->engine->center()))
       return fail(QED_EINVAL, "size must equal the centre tensor size");
     double e = 0.0;
-    int rc = s->engine->energy_grad(psi_device, &e, dE_dpsi_device, dE_dcoupling);
+    double dc[qed::N_CLASSES];
+    int rc = s->engine->energy_grad(psi_device, &e, dE_dpsi_device, dc);
+    for (int c = 0; c < qed::N_COUPLINGS; ++c) dE_dcoupling[c] = dc[c];
     if (rc) return engine_status(s->engine, rc);
     if (energy) *energy = e;
     return QED_OK;

@@ -636,7 +636,7 @@ void Engine::set_precision(int p) {
 
 Engine::Engine(const Params& p, int chi, uint64_t seed, int precision, cudaStream_t stream)
     : p_(p), chi_(chi), seed_(seed), precision_(precision), stream_(stream) {
-  lat_ = Lattice{p.Lx, p.Ly, p.Lz};
+  lat_ = Lattice{p.Lx, p.Ly, p.Lz, p.boundary == 1};
   const char* v = std::getenv("QED_VALIDATE");
   validate_ = v && v[0] == '1';
   if (const char* ks = std::getenv("QED_KC_SHAPE")) {
@@ -2060,7 +2060,7 @@ int Engine::energy_grad(const double* psi, double* energy, double* grad, double 
   const double* x = psi ? psi : T_[center_];
   double* hx = grad_a_;
   double* htx = grad_b_;
-  double* dv = d_scal_ + 700;   // [0] |psi|^2, [1] psi.H psi, [2..6] classes
+  double* dv = d_scal_ + 700;   // [0] |psi|^2, [1] psi.H psi, [2..7] classes
   int rc = 0;
   launch_dot(x, x, n, d_partial_, dv, stream_);
   if ((rc = apply_heff(x, hx, -1))) return rc;
@@ -2069,14 +2069,15 @@ int Engine::energy_grad(const double* psi, double* energy, double* grad, double 
     if ((rc = apply_heff(x, y_out_, c))) return rc;
     launch_dot(x, y_out_, n, d_partial_, dv + 2 + c, stream_);
   }
-  double host[8];
-  cudaMemcpyAsync(host, dv, 7 * sizeof(double), cudaMemcpyDeviceToHost, stream_);
+  double host[2 + N_CLASSES];
+  cudaMemcpyAsync(host, dv, (2 + N_CLASSES) * sizeof(double), cudaMemcpyDeviceToHost, stream_);
   if (!check(cudaStreamSynchronize(stream_), "energy gradient")) return -3;
   const double nrm = host[0];
   if (!(nrm > 0.0)) { err_ = "energy gradient: zero vector"; return -1; }
   const double e = host[1] / nrm;
   if (energy) *energy = e;
-  const double coupling[N_CLASSES] = {p_.t, p_.m, p_.ge2, p_.cB, p_.nu};
+  // the chemical potentials have no single coupling: dc[CLS_MU] = <H_mu>
+  const double coupling[N_CLASSES] = {p_.t, p_.m, p_.ge2, p_.cB, p_.nu, 1.0};
   for (int c = 0; c < N_CLASSES; ++c)
     dc[c] = coupling[c] != 0.0 ? host[2 + c] / nrm / coupling[c] : std::nan("");
   if (grad) {
@@ -2885,9 +2886,9 @@ int Engine::energy(double* total, double parts[N_CLASSES]) {
     if (rc) return rc;
     launch_dot(T_[center_], tmp_, n, d_partial_, dv + 1 + c, stream_);
   }
-  double host[8];
+  double host[2 + N_CLASSES];
   cudaMemcpyAsync(host, nrm2, sizeof(double), cudaMemcpyDeviceToHost, stream_);
-  cudaMemcpyAsync(host + 1, dv, 6 * sizeof(double), cudaMemcpyDeviceToHost, stream_);
+  cudaMemcpyAsync(host + 1, dv, (1 + N_CLASSES) * sizeof(double), cudaMemcpyDeviceToHost, stream_);
   if (!check(cudaStreamSynchronize(stream_), "energy")) return -3;
   *total = host[1] / host[0];
   for (int c = 0; c < N_CLASSES; ++c) parts[c] = host[2 + c] / host[0];
@@ -2989,9 +2990,9 @@ int Engine::set_couplings(const Params& np) {
     err_ = "set_couplings: the lattice, the boundary and the charge sector are fixed";
     return -1;
   }
-  const double oldc[N_CLASSES] = {p_.t, p_.m, p_.ge2, p_.cB, p_.nu};
-  const double newc[N_CLASSES] = {np.t, np.m, np.ge2, np.cB, np.nu};
-  for (int c = 0; c < N_CLASSES; ++c)
+  const double oldc[N_COUPLINGS] = {p_.t, p_.m, p_.ge2, p_.cB, p_.nu};
+  const double newc[N_COUPLINGS] = {np.t, np.m, np.ge2, np.cB, np.nu};
+  for (int c = 0; c < N_COUPLINGS; ++c)
     if (!std::isfinite(newc[c]) || (oldc[c] == 0.0 && newc[c] != 0.0)) {
       err_ = "set_couplings: a coupling is not finite, or its class was zero at creation (no terms)";
       return -1;
@@ -2999,9 +3000,10 @@ int Engine::set_couplings(const Params& np) {
   // same term list as a fresh model with these couplings; a class switched
   // off keeps its terms with coefficient zero
   Params sub = np;
-  double* subc[N_CLASSES] = {&sub.t, &sub.m, &sub.ge2, &sub.cB, &sub.nu};
-  for (int c = 0; c < N_CLASSES; ++c)
-    if (newc[c] == 0.0) *subc[c] = 1.0;
+  sub.mu = p_.mu;   // the chemical potentials stay as created
+  double* subc[N_COUPLINGS] = {&sub.t, &sub.m, &sub.ge2, &sub.cB, &sub.nu};
+  for (int c = 0; c < N_COUPLINGS; ++c)
+    if (newc[c] == 0.0 && oldc[c] != 0.0) *subc[c] = 1.0;
   std::vector<Term> nt;
   double cst = 0.0;
   build_terms(sub, &nt, &cst);
@@ -3014,7 +3016,8 @@ int Engine::set_couplings(const Params& np) {
       err_ = "set_couplings: term list changed";
       return -1;
     }
-  for (size_t i = 0; i < nt.size(); ++i) terms_[i].coef = newc[nt[i].cls] == 0.0 ? 0.0 : nt[i].coef;
+  for (size_t i = 0; i < nt.size(); ++i)
+    terms_[i].coef = (nt[i].cls < N_COUPLINGS && newc[nt[i].cls] == 0.0) ? 0.0 : nt[i].coef;
   constant_ = cst;
   p_.t = np.t; p_.m = np.m; p_.ge2 = np.ge2; p_.cB = np.cB; p_.nu = np.nu;
   // drop everything that holds a coefficient

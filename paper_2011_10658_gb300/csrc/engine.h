@@ -114,7 +114,7 @@ struct BondOp {
 
 struct BondOps {
   std::unordered_map<int, BondOp> term;
-  double* H[N_CLASSES] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  double* H[N_CLASSES] = {};
   double* Htot = nullptr;
 };
 

@@ -184,6 +184,7 @@ int Lattice::neighbour(int s, int mu, int step) const {
   coords(s, c);
   c[mu] += step;
   const int dims[3] = {Lx, Ly, Lz};
+  if (periodic && dims[mu] > 1) c[mu] = ((c[mu] % dims[mu]) + dims[mu]) % dims[mu];
   if (c[mu] < 0 || c[mu] >= dims[mu]) return -1;
   return index(c[0], c[1], c[2]);
 }
@@ -224,7 +225,7 @@ static OpKey key(int kind, int a = 0, int b = 0) {
 // Eq. (1) + Eq. (16) as coefficient x product of local ops.  Same order as
 // the terms are listed: mass, electric, hopping, plaquette, penalty.
 void build_terms(const Params& p, std::vector<Term>* terms, double* constant) {
-  Lattice lat{p.Lx, p.Ly, p.Lz};
+  Lattice lat{p.Lx, p.Ly, p.Lz, p.boundary == 1};
   terms->clear();
   const int n = lat.n_sites();
   auto push = [&](double coef, int cls, std::vector<std::pair<int, OpKey>> ops) {
@@ -277,6 +278,8 @@ void build_terms(const Params& p, std::vector<Term>* terms, double* constant) {
       for (int k = 0; k < 3; ++k) push(p.nu, CLS_NU, {{x, key(OP_P, 3 + mu, k)}, {y, key(OP_PC, mu, 2 - k)}});
     }
   (void)n_links;
+  // local chemical potentials mu_x psi^dag_x psi_x (diagonal, own class)
+  for (int s = 0; s < n && s < (int)p.mu.size(); ++s) push(p.mu[s], CLS_MU, {{s, key(OP_N)}});
   *constant = 0.0;
 }
 

@@ -40,13 +40,19 @@ struct SiteOp {
 
 struct Params {
   int32_t Lx = 2, Ly = 2, Lz = 2;
-  int32_t boundary = 0;          // 0 = open with dangling half-links
+  int32_t boundary = 0;          // 0 = open with dangling half-links, 1 = periodic
+  // local chemical potentials mu_x (one per site, empty = none): terms
+  // mu_x psi^dag_x psi_x of their own class (Methods: the diagonal local
+  // terms used to pin charges)
+  std::vector<double> mu;
   double t = 1.0, m = 1.0, ge2 = 1.0, cB = 0.5, nu = 10.0;
   int32_t Q = 0;
 };
 
 // Coupling classes, in the order t, m, ge2, cB, nu.
-enum CouplingClass : int { CLS_T = 0, CLS_M = 1, CLS_GE2 = 2, CLS_CB = 3, CLS_NU = 4, N_CLASSES = 5 };
+// N_COUPLINGS scalar couplings; the chemical potentials form one more class.
+enum CouplingClass : int { CLS_T = 0, CLS_M = 1, CLS_GE2 = 2, CLS_CB = 3, CLS_NU = 4, CLS_MU = 5, N_CLASSES = 6 };
+constexpr int N_COUPLINGS = 5;
 
 struct Term {
   double coef = 0.0;
@@ -61,6 +67,9 @@ void build_site_op(int parity, const OpKey& key, SiteOp* out);
 
 struct Lattice {
   int Lx, Ly, Lz;
+  // 1: periodic in every direction with more than one site (a direction of
+  // extent 1 has no links and keeps its dangling half-links)
+  int periodic = 0;
   int n_sites() const { return Lx * Ly * Lz; }
   int index(int i, int j, int k) const { return i + Lx * (j + Ly * k); }
   void coords(int s, int c[3]) const;

@@ -88,7 +88,7 @@ def test_local_op_errors(q):
 
 
 KIND = {"M": 1, "Md": 2, "C": 3, "P": 4, "n": 5, "E2": 6, "PC": 8}
-CLS = {"t": 0, "m": 1, "ge2": 2, "cB": 3, "nu": 4}
+CLS = {"t": 0, "m": 1, "ge2": 2, "cB": 3, "nu": 4, "mu": 5}
 
 
 def _oracle_terms(p):
@@ -108,19 +108,28 @@ def _oracle_terms(p):
                 ops.append((s, KIND[k], 0, 0))
             else:
                 ops.append((s, KIND[k], sum(1 << j for j in key[1]), 0))
-        rows.append((tm.coef, CLS[tm.cls], tuple(ops)))
+        # factors act on different sites and commute: compare them in site order
+        rows.append((tm.coef, CLS[tm.cls], tuple(sorted(ops))))
     return rows, const
 
 
-@pytest.mark.parametrize("L,Q", [((2, 1, 1), 0), ((2, 2, 1), 1), ((2, 2, 2), 0), ((4, 4, 4), 4)])
-def test_term_list_equal(q, L, Q):
+@pytest.mark.parametrize("L,Q,boundary,with_mu", [((2, 1, 1), 0, 0, False), ((2, 2, 1), 1, 0, False),
+                                                  ((2, 2, 2), 0, 0, False), ((4, 4, 4), 4, 0, False),
+                                                  ((2, 1, 1), 0, 1, False), ((2, 2, 1), 0, 1, True),
+                                                  ((2, 2, 2), 0, 1, False), ((4, 2, 2), 2, 1, True),
+                                                  ((4, 4, 4), 0, 1, False), ((4, 4, 4), 0, 0, True)])
+def test_term_list_equal(q, L, Q, boundary, with_mu):
     kw = dict(t=0.9, m=-0.4, ge2=1.3, cB=0.35, nu=12.0, Q=Q)
-    m = q.Model(*L, **kw)
+    n = L[0] * L[1] * L[2]
+    mu = tuple(np.round(np.random.default_rng(n).uniform(-2, 2, n), 3)) if with_mu else ()
+    if with_mu:
+        mu = tuple(0.0 if i % 5 == 0 else float(v) for i, v in enumerate(mu))   # zeros give no term
+    m = q.Model(*L, boundary=boundary, mu=(mu if with_mu else None), **kw)
     coef, cls, nops, ops = m.terms()
     native = []
     for i in range(len(coef)):
         native.append((coef[i], int(cls[i]), tuple(tuple(int(v) for v in ops[i, f]) for f in range(nops[i]))))
-    ref, const = _oracle_terms(omodel.Params(*L, **kw))
+    ref, const = _oracle_terms(omodel.Params(*L, boundary=boundary, mu=mu, **kw))
     assert native == ref
     assert m.info()["constant"] == const
 
@@ -149,7 +158,11 @@ def test_model_errors(q):
     with pytest.raises(QedError):
         q.Model(3, 2, 2)
     with pytest.raises(QedError):
-        q.Model(2, 2, 2, boundary=1)
+        q.Model(2, 2, 2, boundary=2)
+    with pytest.raises(QedError):
+        q.Model(2, 2, 2, mu=[0.5] * 7)
+    with pytest.raises(QedError):
+        q.Model(2, 2, 2, mu=[0.5] * 7 + [float("inf")])
     with pytest.raises(QedError):
         q.Model(2, 2, 2, t=float("nan"))
 

@@ -77,6 +77,9 @@ def test_set_couplings_rejects_a_class_absent_at_creation(q):
     s = q.TTN(q.Model(2, 2, 1, Q=0, **c), 8, seed=0, precision="fp64")
     with pytest.raises(q.QedError):
         s.set_couplings(**dict(c, cB=0.5))
+    # keeping the absent class at zero while another coupling changes is fine
+    s.set_couplings(**dict(c, nu=4.0))
+    s.sweep(1, tol=1e-10)
     s.close()
 
 

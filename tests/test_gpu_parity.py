@@ -38,11 +38,17 @@ def max_rel(a, b):
     return float(np.max(np.abs(a - b)) / max(1e-300, np.max(np.abs(b))))
 
 
+# capacitor plates on 2x2x2: mu = -1.5 on the x = 0 face, +1.5 on x = 1
+PLATES = tuple(-1.5 if s % 2 == 0 else 1.5 for s in range(8))
 CASES = [((2, 1, 1), 8, 0, {}), ((2, 2, 1), 12, 3, dict(t=0.8, m=0.3, ge2=1.5, cB=0.9, nu=20.0, Q=1)),
-         ((2, 2, 2), 8, 0, dict(t=1.0, m=1.0, ge2=1.0, cB=0.5, nu=10.0, Q=0))]
+         ((2, 2, 2), 8, 0, dict(t=1.0, m=1.0, ge2=1.0, cB=0.5, nu=10.0, Q=0)),
+         ((2, 2, 1), 12, 2, dict(t=1.0, m=0.5, ge2=1.0, cB=0.5, nu=10.0, Q=0, boundary=1)),
+         ((2, 2, 2), 8, 1, dict(t=1.0, m=1.0, ge2=1.0, cB=0.5, nu=10.0, Q=0, boundary=1)),
+         ((2, 2, 2), 8, 4, dict(t=1.0, m=0.5, ge2=1.0, cB=0.5, nu=10.0, Q=0, mu=PLATES))]
 
 
-@pytest.fixture(scope="module", params=CASES, ids=["2x1x1", "2x2x1", "2x2x2"])
+@pytest.fixture(scope="module", params=CASES,
+                ids=["2x1x1", "2x2x1", "2x2x2", "2x2x1-periodic", "2x2x2-periodic", "2x2x2-plates"])
 def pair(request, q):
     L, chi, seed, kw = request.param
     return make_pair(q, L, chi, seed, **kw)
@@ -117,7 +123,12 @@ def test_sweep_matches_oracle_node_by_node(pair):
         ref_e.append(ref.optimize_node(idx, tol=1e-12))
         got_e.append(s.optimize_node(idx, tol=1e-12, max_krylov=64))
     ref_e, got_e = np.array(ref_e), np.array(got_e)
-    assert np.max(np.abs(got_e - ref_e) / np.abs(ref_e)) < REL_FP64, (got_e, ref_e)
+    # relative to the sweep's energy scale: from a penalty-dominated start
+    # (|E| ~ 150) to a final |E| ~ 1, the eigenvectors are fixed only to the
+    # solver tolerance times that scale (the oracle's own 2x2x2 periodic sweep
+    # moves by 1e-10 absolute between tolerances 1e-12 and 1e-14)
+    scale = np.maximum(np.abs(ref_e), np.max(np.abs(ref_e)))
+    assert np.max(np.abs(got_e - ref_e) / scale) < REL_FP64, (got_e, ref_e)
 
 
 def test_energy_classes_and_observables(pair):
@@ -125,10 +136,12 @@ def test_energy_classes_and_observables(pair):
     # after the node-by-node sweep of the previous test, both states agree
     et, ew, parts = s.energy()
     want_total = ottn.expectation(ref, p)
-    assert abs(et - want_total) < REL_FP64 * abs(want_total)
+    # the sweep's energy scale, as in the node-by-node comparison
+    scale = max([abs(want_total)] + [abs(e) for e in ref.energies])
+    assert abs(et - want_total) < REL_FP64 * scale
     for c in ("t", "m", "ge2", "cB", "nu"):
         want = ottn.expectation(ref, omodel.class_only(p, c))
-        assert abs(parts[c] - want) < 1e-9 * max(1.0, abs(want_total)), c
+        assert abs(parts[c] - want) < 1e-9 * max(1.0, scale), c
     assert abs(ew - (et - parts["nu"])) < 1e-12 * abs(et)
     obs = ref.observables()
     sc = s.measure("scalars")
@@ -138,6 +151,9 @@ def test_energy_classes_and_observables(pair):
     np.testing.assert_allclose(s.measure("phi"), obs["phi"], atol=1e-9)
     np.testing.assert_allclose(s.measure("elink"), obs["E_link"], atol=1e-9)
     np.testing.assert_allclose(s.measure("sigma"), obs["sigma"], atol=1e-9)
+    # the chemical-potential class: E_total minus the five coupling classes
+    mu = np.array(p.mu) if p.mu else np.zeros(len(obs["phi"]))
+    assert abs(et - sum(parts.values()) - float(mu @ np.array(s.measure("phi")))) < 1e-10 * max(1.0, abs(et))
 
 
 @pytest.mark.parametrize("shape", ["16", "32", "64", "1664", "6416"])
@@ -174,3 +190,29 @@ def test_plain_workload_matches_stored_oracle_sweep(q):
     for _, node, e in rows:
         got = s.optimize_node(int(node), tol=1e-12, max_krylov=64)
         assert abs(got - float(e)) < REL_FP64 * abs(float(e)), (node, got, e)
+
+
+def test_periodic_ring_matches_configuration_ed(q):
+    """2x1x1 periodic (two links between the sites): the library's
+    single-node sweep equals the configuration-basis diagonalisation."""
+    kw = dict(t=0.7, m=-0.3, ge2=2.0, cB=0.25, nu=10.0, Q=0, boundary=1)
+    s = q.TTN(q.Model(2, 1, 1, **kw), 8, seed=0)
+    st = s.sweep(1, tol=1e-12, max_krylov=64)
+    e_ed = ed.config_ed(omodel.Params(2, 1, 1, **kw))
+    assert abs(st["energy"] - e_ed) < REL_FP64 * abs(e_ed)
+
+
+def test_periodic_plates_mixed_precision_updates(q):
+    """4x2x2 periodic with potentials on two faces, chi = 16: every node
+    update of one sweep in split TF32 equals the FP64 update within the
+    mixed gate (identical seeded start)."""
+    mu = [(-2.0 if s % 4 == 0 else (2.0 if s % 4 == 3 else 0.0)) for s in range(16)]
+    kw = dict(t=1.0, m=0.5, ge2=1.0, cB=0.5, nu=10.0, Q=0, boundary=1, mu=mu)
+    a = q.TTN(q.Model(4, 2, 2, **kw), 16, seed=6, precision="fp64")
+    b = q.TTN(q.Model(4, 2, 2, **kw), 16, seed=6, precision="tf32x3")
+    for node in a.model.sweep_order():
+        ea = a.optimize_node(int(node), tol=1e-10, max_krylov=64)
+        eb = b.optimize_node(int(node), tol=1e-10, max_krylov=64)
+        assert abs(ea - eb) < 1e-6 * abs(ea), (node, ea, eb)
+    a.close()
+    b.close()
