@@ -204,15 +204,20 @@ def test_periodic_ring_matches_configuration_ed(q):
 
 def test_periodic_plates_mixed_precision_updates(q):
     """4x2x2 periodic with potentials on two faces, chi = 16: every node
-    update of one sweep in split TF32 equals the FP64 update within the
-    mixed gate (identical seeded start)."""
+    update of one sweep in split TF32 equals the FP64 update of the same
+    state (same centre tensor and environment) within the mixed gate; the
+    sweep then continues from the mixed update."""
     mu = [(-2.0 if s % 4 == 0 else (2.0 if s % 4 == 3 else 0.0)) for s in range(16)]
     kw = dict(t=1.0, m=0.5, ge2=1.0, cB=0.5, nu=10.0, Q=0, boundary=1, mu=mu)
-    a = q.TTN(q.Model(4, 2, 2, **kw), 16, seed=6, precision="fp64")
-    b = q.TTN(q.Model(4, 2, 2, **kw), 16, seed=6, precision="tf32x3")
-    for node in a.model.sweep_order():
-        ea = a.optimize_node(int(node), tol=1e-10, max_krylov=64)
-        eb = b.optimize_node(int(node), tol=1e-10, max_krylov=64)
+    s = q.TTN(q.Model(4, 2, 2, **kw), 16, seed=6, precision="tf32x3")
+    for node in s.model.sweep_order():
+        node = int(node)
+        s.move_center(node)
+        t0 = s.node_export(node)
+        s.set_precision("fp64")
+        ea = s.optimize_node(node, tol=1e-10, max_krylov=64)
+        s.node_import(node, t0)
+        s.set_precision("tf32x3")
+        eb = s.optimize_node(node, tol=1e-10, max_krylov=64)
         assert abs(ea - eb) < 1e-6 * abs(ea), (node, ea, eb)
-    a.close()
-    b.close()
+    s.close()
