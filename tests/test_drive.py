@@ -128,3 +128,12 @@ def test_oracle_set_couplings_switches_a_class_off(swept_2x2x1):
     want = sum(ottn.expectation(s, omodel.class_only(p, c)) for c in ("t", "m", "ge2", "nu"))
     assert abs(e - want) < 1e-11 * abs(want)
     s.set_couplings(cB=0.5)
+
+
+@pytest.mark.parametrize("L,boundary", [((4, 4, 4), 0), ((4, 2, 2), 1), ((2, 2, 1), 1)])
+def test_bench_link_order_matches_the_lattice(L, boundary):
+    """The capacitor profile E_c(d) of bench.py indexes ttn_measure's link
+    list by (site, direction) in the lattice's link order."""
+    import bench
+    want = [(x, mu) for (x, mu, _) in omodel.lattice(omodel.Params(*L, boundary=boundary)).links()]
+    assert bench._links(L, boundary == 1) == want
