@@ -25,6 +25,13 @@ time each path needs to reach a common energy.
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 workload (H_eff x at bottom node 0 with synthetic environment operators of
 the right shapes; algorithmic flops counted by the oracle itself).
+
+Other configurations (--mode): batch (independent 4x4x4 chi=48 problems
+swept together against one after another), scale (8x8x8 chi=128 Q=32, two
+sweeps per g^2), physics (finite-density, periodic zero-charge and
+capacitor workloads with the driven penalty), heff and profile (profiling
+aids: products at one node, or one product / move / product inside a
+profiler window).
 """
 import argparse
 import json
