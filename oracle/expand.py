@@ -21,7 +21,12 @@ sectors are kept (values at or below cutoff times the largest are dropped),
 which fixes the new sector dimensions of b; A becomes the isometry U and
 S V^T is absorbed into t.
 
-Readings: only the first bond of each centre path is expanded (the one the
+Readings: a column of P keeps its charge even where the neighbour's other
+legs cannot form it yet (its block in t starts empty); that is how sectors
+grow through a node whose two other bonds must match, such as the root
+(two-step adaptation: one bond gains the sector empty, the next expanded
+move fills the other); only the first bond of each centre path is expanded
+(the one the
 freshly optimised tensor leaves through); the later bonds of the path are
 crossed by the same SVD move with alpha = 0, so every bond dimension follows
 the rank of its tensors (a truncated bond elsewhere can leave a bond with

@@ -80,3 +80,23 @@ def test_truncation_respects_chi_max(e_ed):
     es = expand.sweep_expanded(s, 1e-10, 1e-3, 3)
     assert all(sum(b.values()) <= 3 for b in s.bonds)
     assert es[-1] > e_ed
+
+
+@pytest.mark.parametrize("start,target,boundary", [(4, 0, 0), (4, 6, 0), (1, 4, 1)])
+def test_expanded_move_deep_tree(start, target, boundary):
+    """2x2x2 (three layers), open and periodic: untruncated expanded moves
+    down from a middle node, up to the root and up from a bottom node keep
+    the state; the operators rebuilt on the new bond give the same H_eff
+    expectation as a from-scratch recomputation."""
+    p = model.Params(2, 2, 2, t=1.0, m=1.0, ge2=1.0, cB=0.5, nu=10.0, Q=0, boundary=boundary)
+    s = ttn.TTN(p, 4, 1)
+    s.move_to(start)
+    e0 = s.energy_at_center()
+    expand.expand_move(s, target, 0.05, 1000, 0.0)
+    assert abs(s.energy_at_center() - e0) < 1e-11 * abs(e0)
+    # back to the root with SVD moves (a new sector may still be empty on
+    # one side, which a plain QR move cannot factorise), then every bond
+    # operator recomputed from scratch
+    for nxt in s.path(s.center, len(s.nodes) - 1)[1:]:
+        expand.expand_move(s, nxt, 0.0, 1000)
+    assert abs(ttn.expectation(s, p) - e0) < 1e-11 * abs(e0)
