@@ -190,15 +190,24 @@ def probe_peaks(device):
 
 
 # ---------------------------------------------------------------- oracle sample
+def _oracle_tree():
+    from oracle import model as omodel
+    from oracle import ttn as ottn
+    c = workloads.qed_couplings(G2)
+    return ottn.TTN(omodel.Params(*L, Q=Q, **c), CHI, SEED, build_ops=False)
+
+
 def _oracle_with_random_env(node):
     """Oracle TTN of the workload with synthetic environment operators of
     the right shapes at `node` (the oracle's cost depends on shapes only)."""
     import numpy as np
-    from oracle import model as omodel
-    from oracle import ttn as ottn
-    c = workloads.qed_couplings(G2)
-    ref = ottn.TTN(omodel.Params(*L, Q=Q, **c), CHI, SEED, build_ops=False)
-    rng = np.random.default_rng(0)
+    ref = _oracle_tree()
+    _set_random_env(ref, node, np.random.default_rng(0))
+    return ref
+
+
+def _set_random_env(ref, node, rng):
+    """Random environment and child operators of the right shapes at node."""
     dim = ref.T[node].shape[2]
     env = {}
     for k, tm in enumerate(ref.terms):
@@ -215,7 +224,39 @@ def _oracle_with_random_env(node):
             Hc = rng.standard_normal((d, d))
             ops["H"] = Hc + Hc.T
             ref.up[cid] = ops
-    return ref
+
+
+def oracle_upper_sample():
+    """Seconds of one FP64 oracle H_eff x at the first node of every upper
+    layer of the workload's tree (random environments of the right shapes,
+    one oracle tree for all), with the number of nodes in each layer."""
+    import numpy as np
+    ref = _oracle_tree()
+    rng = np.random.default_rng(1)
+    out = []
+    for layer in sorted({nd.layer for nd in ref.nodes if nd.layer > 0}):
+        ids = [nd.index for nd in ref.nodes if nd.layer == layer]
+        node = ids[0]
+        _set_random_env(ref, node, rng)
+        terms = ref.heff_terms(node)
+        X = ref.T[node]
+        ref.heff_apply(node, X, terms)
+        t0 = time.time()
+        ref.heff_apply(node, X, terms)
+        out.append((node, len(ids), time.time() - t0))
+    return out
+
+
+def extrapolated_oracle_sweep(kt, steps, t_bottom, upper):
+    """Oracle seconds for the products of one sweep: the sweep's bottom-node
+    products (tensor-core and residual-correction) at the timed bottom-node
+    rate, its upper-node products at the node-weighted mean of the timed
+    upper layers.  Operator updates and the eigensolver's own work are not
+    included."""
+    n_bottom = (kt["tc_heff"]["launches"] + kt["heff_simt_bottom"]["launches"]) / steps
+    n_upper = kt["heff_simt_upper"]["launches"] / steps
+    t_upper = sum(n * t for (_, n, t) in upper) / max(1, sum(n for (_, n, _) in upper))
+    return n_bottom * t_bottom + n_upper * t_upper, n_bottom, n_upper, t_upper
 
 
 def oracle_sample(n_matvecs=None, budget_s=20.0, node=0):
@@ -464,11 +505,15 @@ def run_native(args):
         cpu = {"value": f0 / t_mv / 1e12, "unit": "TFLOP/s", "cores": threads, "kind": "oracle", "sample": sample,
                "single_thread": ({"seconds_per_product": one["t"], "tflops": f0 / one["t"] / 1e12}
                                  if "t" in one else one)}
-        # products of one sweep at the oracle's rate (a lower bound of an
+        # products of one sweep at the oracle's speed (a lower bound of an
         # oracle sweep: operator updates and the eigensolver's own work not
-        # included), extrapolated from the timed bottom-node products
-        per_sweep = value * (elapsed_ms / args.steps * 1e-3) * 1e12
-        cpu["sweep_seconds_extrapolated"] = per_sweep / (f0 / t_mv)
+        # included), extrapolated from timed bottom- and upper-node products
+        upper = oracle_upper_sample()
+        sweep_s, n_b, n_u, t_u = extrapolated_oracle_sweep(kt, args.steps, t_mv, upper)
+        cpu["sweep_seconds_extrapolated"] = sweep_s
+        cpu["extrapolation"] = (f"{n_b:.0f} bottom-node products per sweep x {t_mv:.3f} s + {n_u:.0f} upper-node "
+                                f"products x {t_u:.4f} s (one node per upper layer timed, weighted by the layer's "
+                                f"node count: " + ", ".join(f"node {nd} {t:.4f} s" for (nd, _, t) in upper) + ")")
 
     if rank == 0:
         total_mv = sum(st["matvecs"] for st in stats)
