@@ -137,3 +137,21 @@ def test_bench_link_order_matches_the_lattice(L, boundary):
     import bench
     want = [(x, mu) for (x, mu, _) in omodel.lattice(omodel.Params(*L, boundary=boundary)).links()]
     assert bench._links(L, boundary == 1) == want
+
+
+def test_oracle_driven_run_two_sites():
+    """2x1x1, one node: the driven run's last energy is the two-site closed
+    form (the link constraint is exact once nu is large enough, R6), delta_L
+    vanishes, and the records follow the schedule (nu 0.5, 3.5, 6.5, 9.5,
+    then 10 until two energies agree)."""
+    c = dict(t=1.0, m=1.0, ge2=1.0, cB=0.5, nu=0.5)
+    st = ottn.TTN(omodel.Params(2, 1, 1, Q=0, **c), 8, 0)
+    recs, conv = odrive.run(st, nu_start=0.5, nu_step=3.0, quad_coef=0.25, nu_max=10.0, tol_start=1e-10,
+                            tol_factor=0.1, tol_final=1e-12, conv_rel=1e-10, rise_rel=1e-9, min_final_sweeps=2,
+                            max_sweeps=8)
+    assert conv
+    assert [r["nu"] for r in recs][:5] == [0.5, 3.5, 6.5, 9.5, 10.0]
+    exact = 0.25 - np.sqrt(41.0) / 4.0
+    assert abs(recs[-1]["energy"] - exact) < 1e-10
+    assert recs[-1]["delta_L"] < 1e-10
+    assert abs(recs[-1]["energy_without_penalty"] - recs[-1]["energy"]) < 1e-10
