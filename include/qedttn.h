@@ -180,9 +180,9 @@ int ttn_set_couplings(ttn_state *s, const double couplings[5]);
  * sweep to sweep).  The penalty nu of sweep s:
  *   linear stage:    nu_0 = nu_start, nu_{s+1} = nu_s + nu_step, until the
  *                    energy <H + H_pen> after a sweep exceeds the previous
- *                    sweep's by more than rise_rel |E_prev| (the "slight
- *                    rise"; rise_rel keeps rounding from counting), which
- *                    ends the stage;
+ *                    sweep's by more than rise_rel |E_prev| (a small
+ *                    increase; rise_rel keeps rounding from counting),
+ *                    which ends the stage;
  *   quadratic stage: nu = nu_switch + quad_coef * nu_step * k^2 for the k-th
  *                    sweep after the switch (k = 1, 2, ...; quad_coef < 1
  *                    makes the first increments smaller than nu_step);

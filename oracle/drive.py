@@ -5,7 +5,7 @@ Methods, "Numerical Convergence": the link constraint L = 2 is imposed by
 the penalty nu sum (1 - delta_{2,L}) of Eq. (16).  A large nu from the first
 sweep can trap the variational search, so nu is driven in three stages:
   (i)   from a small value and a random state, nu grows linearly from sweep
-        to sweep until the energy shows a slight rise;
+        to sweep until the energy starts to go up;
   (ii)  then nu grows quadratically, so that in the sweeps right after the
         switch the increments are smaller than in the linear stage;
   (iii) once nu reaches the wanted maximum it stays there, and sweeps run
