@@ -466,6 +466,10 @@ def run_native(args):
                 "algorithmic_flops_per_launch": d["flops_alg"] / max(1, d["launches"]),
                 "executed_flops_per_launch": d["flops_exec"] / max(1, d["launches"]),
                 "share_of_step": d["ms"] / elapsed_ms}
+    # the same fraction against the measured BF16 peak of the pool times the
+    # nominal dense ratio of this dtype (1.1/2.25 for TF32)
+    nominal = pk["bf16_tflops_sustained"] * (1.0 if tensor_dtype == "bf16" else 1.1 / 2.25)
+    roofline["peak_from_measured_bf16"] = {"tflops": nominal, "frac": achieved / nominal, "source": src}
     largest = max(classes, key=lambda k: classes[k]["ms"])
 
     # end to end through the public API with host buffers: tensors in from
