@@ -100,3 +100,17 @@ def test_expanded_move_deep_tree(start, target, boundary):
     for nxt in s.path(s.center, len(s.nodes) - 1)[1:]:
         expand.expand_move(s, nxt, 0.0, 1000)
     assert abs(ttn.expectation(s, p) - e0) < 1e-11 * abs(e0)
+
+
+@pytest.mark.parametrize("Q", [1, -1])
+def test_expansion_at_finite_charge(Q):
+    """2x2x1 with one net charge: from chi = 2 one expanded sweep reaches the
+    configuration-basis ground energy of that charge sector, with bond
+    sectors that are no longer symmetric about zero."""
+    p = model.Params(2, 2, 1, t=0.8, m=0.3, ge2=1.5, cB=0.9, nu=20.0, Q=Q)
+    s = ttn.TTN(p, 2, 3)
+    es = expand.sweep_expanded(s, 1e-10, 1e-3, 16)
+    e_ed = ed.config_ed(p)
+    assert abs(es[-1] - e_ed) < 1e-10 * abs(e_ed)
+    assert s.bonds[-1] == {Q: 1}
+    assert s.bonds[1].get(Q, 0) > s.bonds[1].get(-Q, 0)
